@@ -1,0 +1,188 @@
+/*
+ * torontonian.h -- C ABI of the GB300 (sm_103a) Torontonian library.
+ *
+ * The library evaluates the Torontonian of a threshold-detection Gaussian
+ * boson sampling click pattern (paper Sec. 3.1, Eq. 2):
+ *
+ *     Tor(O) = sum_{Z subset of [k]} (-1)^(k-|Z|) / sqrt(det(I - O_Z))
+ *
+ * where O is the 2k x 2k real-quadrature matrix O_S of the clicked modes,
+ * O = I - Sigma^-1 (the paper's A), and O_Z keeps the x and p rows/columns
+ * of the modes in Z (selection rule under Eq. 1).  The click probability of
+ * Eq. 1 is p(S) = Tor(O_S) / sqrt(det Sigma).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are FP64, row-major, with a leading dimension `ld` (in
+ *     elements, ld >= 2k).  TOR_LAYOUT_XXPP is the paper's order (rows
+ *     0..k-1 = x of the clicked modes, k..2k-1 = p); TOR_LAYOUT_XPXP is
+ *     mode-interleaved (x_0, p_0, x_1, p_1, ...).
+ *   - Pointers marked `dev` are device memory on the context's GPU, owned by
+ *     the caller; pointers marked `host` are host memory owned by the caller.
+ *     The library keeps no pointer after a call returns.
+ *   - The library allocates device memory only inside a context (workspace
+ *     that grows on demand and is released by tor_destroy).
+ *   - Calls taking a stream enqueue work on it.  Entry points that write a
+ *     `host` result synchronise that stream before returning; the others
+ *     return after enqueueing and their `dev` results are valid once the
+ *     stream has been synchronised.
+ *   - Every entry point returns a TOR_* status; no C++ exception crosses the
+ *     ABI.  tor_last_error() gives a message for the calling thread.
+ *   - k = 0 gives Tor = 1 (only the empty set).  k > TOR_MAX_K is TOR_EINVAL.
+ *   - A matrix for which some I - O_Z is not positive definite (a pivot
+ *     <= 0, or not finite) gives TOR_ENOTPD and the result's status field is
+ *     set; the numeric fields are then meaningless.
+ *
+ * Accuracy
+ *   Subset terms t_Z = 1/sqrt(det(I - O_Z)) are computed in the tier's
+ *   arithmetic (FP64, or double-double) and summed EXACTLY in 256-bit
+ *   fixed point, so the only error is the per-term rounding.  Each result
+ *   carries sum_abs = sum_Z t_Z (condition number kappa = sum_abs/|Tor|) and
+ *   err_est = gamma * u_tier * sum_abs, an a-posteriori bound on |error|.
+ */
+#ifndef TORONTONIAN_H
+#define TORONTONIAN_H
+
+#include <stdint.h>
+#include <stddef.h>
+#include <cuda_runtime.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TOR_MAX_K 64
+
+enum {
+    TOR_OK = 0,
+    TOR_EINVAL = 1,     /* bad argument (size, pointer, enum) */
+    TOR_ENOTPD = 2,     /* some I - O_Z not positive definite */
+    TOR_ECUDA = 3,      /* a CUDA runtime call failed */
+    TOR_ETIMEOUT = 4,   /* a device-side wait exceeded its spin limit */
+    TOR_EPREC = 5,      /* the result's a-posteriori error exceeds the requested tolerance */
+    TOR_ENOMEM = 6      /* workspace allocation failed */
+};
+
+enum { TOR_PREC_AUTO = 0, TOR_PREC_FP64 = 1, TOR_PREC_DD = 2 };
+enum { TOR_LAYOUT_XXPP = 0, TOR_LAYOUT_XPXP = 1 };
+
+typedef struct tor_ctx tor_ctx;
+
+/* Tor as a double-double hi + lo, with its error model. */
+typedef struct {
+    double hi, lo;      /* Tor = hi + lo */
+    double sum_abs;     /* sum_Z t_Z (>= |Tor|) */
+    double err_est;     /* a-posteriori bound on |computed - exact| */
+    int tier;           /* TOR_PREC_FP64 or TOR_PREC_DD: arithmetic actually used */
+    int status;         /* TOR_OK or TOR_ENOTPD for this instance */
+} tor_result;
+
+/* FP32 bound pass output (paper Sec. 5.1 bounds, Eq. bitlen of Sec. 5.4). */
+typedef struct {
+    float log_tmax;       /* ln t_max = -1/2 ln det(I - O): the largest term (Sec. 5.1 upper bound) */
+    float log_tor_est;    /* ln of the product estimate prod_j (tau_j - 1) of Tor */
+    float log_kappa_est;  /* ln of the estimated condition number sum t / |Tor| */
+    float bits_needed;    /* log2 kappa_est + log2(gamma) + log2(1/tol) */
+    int tier;             /* TOR_PREC_FP64 or TOR_PREC_DD */
+} tor_bound;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`.  Returns TOR_OK or an error. */
+int tor_create(tor_ctx **ctx, int device);
+
+/* Release the context and its workspace (NULL is ignored). */
+void tor_destroy(tor_ctx *ctx);
+
+/* Message of the last error raised on the calling thread ("" if none). */
+const char *tor_last_error(void);
+
+/* Launch shape used by the DFS kernels: threads per block and blocks per SM
+ * (0 = library default).  Takes effect on the next call. */
+int tor_set_launch(tor_ctx *ctx, int threads_per_block, int blocks_per_sm);
+
+/* Chunk depth d used by tor_single: chunks fix the top d modes of the subset
+ * mask and each walks the 2^(k-d) subsets of the remaining modes.  -1 selects
+ * the library's automatic choice (the default). */
+int tor_set_chunk_bits(tor_ctx *ctx, int chunk_bits);
+
+/* --------------------------------------------------------------- Tor calls */
+
+/*
+ * tor_single: Tor of one 2k x 2k matrix (Eq. 2).
+ *   O     dev  2k x 2k FP64, leading dimension ld, in `layout` order.
+ *   prec  TOR_PREC_FP64, TOR_PREC_DD, or TOR_PREC_AUTO (the FP32 bound pass
+ *         of tor_bounds picks the tier for tolerance `tol`).
+ *   out   host result; the call synchronises `stream`.
+ * The 2^k subsets are split into equal prefix chunks (the high modes of the
+ * subset mask fixed per chunk, Algorithm 1's balanced partition) walked
+ * depth-first so that each subset's factor extends its parent's.
+ */
+int tor_single(tor_ctx *ctx, const double *O, int k, int ld, int layout, int prec,
+               double tol, cudaStream_t stream, tor_result *out);
+
+/*
+ * tor_single_async: as tor_single, but the result goes to device memory
+ * `out_dev` and the call returns after enqueueing (capturable in a CUDA
+ * graph once the workspace has been sized by an earlier call with the same
+ * k and precision).  prec must be TOR_PREC_FP64 or TOR_PREC_DD.
+ */
+int tor_single_async(tor_ctx *ctx, const double *O, int k, int ld, int layout, int prec,
+                     cudaStream_t stream, tor_result *out_dev);
+
+/*
+ * tor_chunks: partial sums over a range of prefix chunks, for sharding the
+ * 2^k subsets across processes or calls, resuming long runs, and checking
+ * sampled chunks against an independent evaluation.
+ *   chunk_bits  d: chunk c covers the subset masks [c 2^(k-d), (c+1) 2^(k-d)),
+ *               i.e. modes k-d..k-1 are fixed by the bits of c.
+ *   c_begin, c_end  the chunk range [c_begin, c_end) to evaluate.
+ *   part_dev    dev, (c_end - c_begin) x 8 uint64: per chunk the exact sum of
+ *               (-1)^(k-|Z|) t_Z and of t_Z, each a 256-bit two's-complement
+ *               fixed-point number with 128 fractional bits, little-endian
+ *               64-bit limbs (limbs 0..3 = signed sum, 4..7 = sum_abs).
+ *   Partials of disjoint ranges add exactly (integer addition), so any split
+ *   gives the same total bit for bit.
+ */
+int tor_chunks(tor_ctx *ctx, const double *O, int k, int ld, int layout, int prec,
+               int chunk_bits, uint64_t c_begin, uint64_t c_end, cudaStream_t stream,
+               uint64_t *part_dev);
+
+/* Convert one 256-bit fixed-point pair (8 limbs as written by tor_chunks,
+ * possibly summed over shards) to a tor_result (host, no GPU needed). */
+int tor_fixed_to_result(const uint64_t *limbs8, int k, int tier, tor_result *out);
+
+/*
+ * tor_batch: Tor of n matrices of different k in one launch sequence.
+ *   O     dev  array of n device pointers (each 2k_i x 2k_i FP64).
+ *   k,ld  dev  arrays of n ints.
+ *   out   dev  n results.
+ */
+int tor_batch(tor_ctx *ctx, const double *const *O, const int *k, const int *ld, int n,
+              int layout, int prec, double tol, cudaStream_t stream, tor_result *out);
+
+/*
+ * tor_bounds: FP32 bound pass (paper Sec. 5.1, Eq. upbound/lowbound; Sec. 5.4
+ * Eq. bitlen) for n matrices; picks the tier needed for tolerance `tol`.
+ *   O, k, ld  dev arrays as for tor_batch.   out  dev, n bounds.
+ */
+int tor_bounds(tor_ctx *ctx, const double *const *O, const int *k, const int *ld, int n,
+               int layout, double tol, cudaStream_t stream, tor_bound *out);
+
+/* -------------------------------------------------------------- utilities */
+
+/* Kernel timing: when `on`, the walk kernel of every later call is bracketed
+ * by CUDA events recorded on that call's stream. */
+int tor_set_timing(tor_ctx *ctx, int on);
+
+/* Duration in ms of the walk kernel of the most recent timed call (waits for
+ * that kernel to finish).  TOR_EINVAL if no timed call was made. */
+int tor_walk_time(tor_ctx *ctx, float *ms);
+
+/* Measured FP64 FMA throughput of this GPU (DFMA per second), from a
+ * dependent-chain-free DFMA loop over all SMs; the roofline denominator. */
+int tor_fp64_peak(tor_ctx *ctx, double *dfma_per_s, double *sm_clock_hz);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TORONTONIAN_H */

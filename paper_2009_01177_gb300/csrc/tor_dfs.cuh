@@ -1,0 +1,317 @@
+// tor_dfs.cuh -- depth-first subset walk for the Torontonian (Eq. 2).
+//
+// Work split (Algorithm 1's balanced partition, GB300 form): the 2^k subset
+// masks are cut into 2^d equal chunks; chunk c fixes the membership of the
+// high modes r1..k-1 (r1 = k - d) by the bits of c and enumerates every subset
+// of the low modes 0..r1-1, i.e. the masks [c 2^r1, (c+1) 2^r1).  One thread
+// owns one chunk at a time, so all lanes of a warp walk trees of the same
+// shape in lock step.
+//
+// Per chunk:
+//  1. Chunk root (the GENAZ step of the paper's kernel list, Sec. 7.1): gather
+//     B = I - O over the chunk's fixed modes P0 followed by the low modes and
+//     eliminate the P0 modes; what remains is the Schur complement
+//     S_P0 = B_RR - B_RP0 B_P0^-1 B_P0R over the low modes, and
+//     t_P0 = 1/sqrt(det B_P0) (product of the 2x2 pivot-block factors).
+//  2. Depth-first walk over the prefix tree of subsets of the low modes.  A
+//     node Q holds the Schur complement of B_Q over the modes after max(Q).
+//     Its child Q+{c} needs only the 2x2 block of mode c:
+//        det B_{Q+c} = det B_Q * det S_Q[c,c],   t_{Q+c} = t_Q / sqrt(det S_Q[c,c]),
+//     and the grandchildren need the rank-2 update
+//        S_{Q+c} = S_Q[>c,>c] - S_Q[>c,c] S_Q[c,c]^-1 S_Q[c,>c].
+//     So each subset's factor extends its parent's by one appended block row
+//     (the elimination of Sec. 4.2, done once per tree edge instead of once
+//     per subset), costing about 20 FMA per subset on average instead of
+//     O(k^3).
+//
+// Storage: a symmetric 2r x 2r matrix is kept as its lower triangle in
+// REVERSED packed order: with reversed indices p = 2r-1-i, q = 2r-1-j and
+// p >= q, entry (i, j) lives at p(p+1)/2 + q.  Mode m (0-based, of r) owns
+// rows 2m (x) and 2m+1 (p), i.e. reversed rows 2(r-1-m)+1 and 2(r-1-m).  The
+// trailing block after dropping or eliminating the first modes is then a
+// PREFIX of the storage with the same formula, and every offset an update
+// touches depends only on the child's size rp (number of modes after c):
+//   pivot block   a = (2rp+1, 2rp+1)  b = (2rp+1, 2rp)  d = (2rp, 2rp)
+//   pivot columns u_x[i] = (2rp+1, i), u_p[i] = (2rp, i),  i < 2rp
+//   child entries (i, j), j <= i < 2rp  -> offsets [0, rp(2rp+1))
+// The last child (rp = r-1) therefore overwrites its parent in place.
+//
+// Three storage tiers: subtrees of at most RREG modes are fully unrolled in
+// registers; larger nodes live in a per-thread stack in global memory laid
+// out entry-major ([entry][thread]) so that a warp's accesses coalesce.
+//
+// Accumulation: each t_Z goes exactly into 256-bit fixed point (fixacc.cuh),
+// so the alternating sum adds no rounding error and no FP64 work.
+#pragma once
+#include <cstdint>
+#include "fixacc.cuh"
+#include "dd.cuh"
+
+namespace tor {
+
+__host__ __device__ constexpr int sz(int r) { return r * (2 * r + 1); }
+__host__ __device__ constexpr int ix(int hi, int lo) { return hi * (hi + 1) / 2 + lo; }
+
+// status bits written by the kernels
+enum : int { ST_NOTPD = 1, ST_RANGE = 2 };
+
+// ----------------------------------------------------------- accumulators
+struct Sums {
+  Fx256 tor;   // sum of (-1)^(k-|Z|) t_Z
+  Fx256 sabs;  // sum of t_Z
+  int flags;
+};
+
+// acc += (neg ? -|x| : |x|); tiny magnitudes (< 2^-75) are dropped (their
+// contribution is far below any result's resolution); x must be finite.
+__device__ __forceinline__ void fx_add_signed(Fx256 &acc, double x, bool neg, int &flags) {
+  unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const bool xneg = (bits >> 63) != 0ull;
+  bits &= 0x7FFFFFFFFFFFFFFFull;
+  const int e = (int)(bits >> 52);
+  if (e < 947) return;                      // zero or below 2^-75
+  Fx256 X;
+  if (!fx_from_pos_double(__longlong_as_double((long long)bits), X)) { flags |= ST_RANGE; return; }
+  if (neg != xneg) fx_sub(acc, X); else fx_add(acc, X);
+}
+
+// ------------------------------------------------------------ FP64 tier
+struct TierF64 {
+  using T = double;
+  static constexpr int W = 1;      // doubles per stored entry
+  static constexpr int RREG = 3;   // register-resident subtree size (modes)
+
+  __device__ static __forceinline__ T ld(const double *P, int e, size_t st) { return P[(size_t)e * st]; }
+  __device__ static __forceinline__ void stv(double *P, int e, size_t st, T v) { P[(size_t)e * st] = v; }
+  __device__ static __forceinline__ T one() { return 1.0; }
+  __device__ static __forceinline__ T det2(T a, T b, T d) { return fma(a, d, -(b * b)); }
+  // not (0 < x < inf): integer test on the bit pattern, no FP64 compare
+  __device__ static __forceinline__ bool bad(T x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    return (u - 1ull) >= 0x7FEFFFFFFFFFFFFFull;
+  }
+  // 1/sqrt(x): FP32 seed (22.9 bits), two Newton steps y <- y + y(1/2 - (x/2) y^2) in FP64
+  __device__ static __forceinline__ T rsqrt(T x) {
+    const float xf = __double2float_rn(x);
+    double y;
+    if (xf > 1e-30f && xf < 1e30f) {
+      float yf;
+      asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
+      y = (double)yf;
+    } else {
+      asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    }
+    // x/2 by an exponent decrement (integer pipe); x is a positive normal here
+    const double hx = __longlong_as_double(__double_as_longlong(x) - (1ll << 52));
+    double e = fma(-(hx * y), y, 0.5);
+    y = fma(y, e, y);
+    e = fma(-(hx * y), y, 0.5);
+    y = fma(y, e, y);
+    return y;
+  }
+  __device__ static __forceinline__ T mul(T a, T b) { return a * b; }
+  // pivot coefficients: S_cc^-1 = [[al, -be], [-be, de]] with inv = y^2 = 1/det2
+  __device__ static __forceinline__ void coef(T a, T b, T d, T y, T &al, T &be, T &de) {
+    const T inv = y * y;
+    al = d * inv; be = b * inv; de = a * inv;
+  }
+  // v = S_cc^-1 u
+  __device__ static __forceinline__ void vrow(T al, T be, T de, T ux, T up, T &vx, T &vp) {
+    vx = fma(al, ux, -(be * up));
+    vp = fma(de, up, -(be * ux));
+  }
+  __device__ static __forceinline__ T upd(T s, T vx, T ux, T vp, T up) {
+    return fma(-vp, up, fma(-vx, ux, s));
+  }
+  __device__ static __forceinline__ void acc(Sums &S, T t, bool neg) {
+    fx_add_signed(S.tor, t, neg, S.flags);
+    fx_add_signed(S.sabs, t, false, S.flags);
+  }
+};
+
+// ------------------------------------------------------ double-double tier
+struct TierDD {
+  using T = dd;
+  static constexpr int W = 2;
+  static constexpr int RREG = 2;
+
+  __device__ static __forceinline__ T ld(const double *P, int e, size_t st) {
+    return {P[(size_t)(2 * e) * st], P[(size_t)(2 * e + 1) * st]};
+  }
+  __device__ static __forceinline__ void stv(double *P, int e, size_t st, T v) {
+    P[(size_t)(2 * e) * st] = v.hi;
+    P[(size_t)(2 * e + 1) * st] = v.lo;
+  }
+  __device__ static __forceinline__ T one() { return {1.0, 0.0}; }
+  __device__ static __forceinline__ T det2(T a, T b, T d) { return dd_det2(a, b, d); }
+  __device__ static __forceinline__ bool bad(T x) { return TierF64::bad(x.hi); }
+  __device__ static __forceinline__ T rsqrt(T x) { return dd_rsqrt(x, TierF64::rsqrt(x.hi)); }
+  __device__ static __forceinline__ T mul(T a, T b) { return dd_mul(a, b); }
+  __device__ static __forceinline__ void coef(T a, T b, T d, T y, T &al, T &be, T &de) {
+    const T inv = dd_mul(y, y);
+    al = dd_mul(d, inv); be = dd_mul(b, inv); de = dd_mul(a, inv);
+  }
+  __device__ static __forceinline__ void vrow(T al, T be, T de, T ux, T up, T &vx, T &vp) {
+    vx = dd_add(dd_mul(al, ux), dd_neg(dd_mul(be, up)));
+    vp = dd_add(dd_mul(de, up), dd_neg(dd_mul(be, ux)));
+  }
+  __device__ static __forceinline__ T upd(T s, T vx, T ux, T vp, T up) {
+    return dd_rank2_update(s, vx, ux, vp, up);
+  }
+  __device__ static __forceinline__ void acc(Sums &S, T t, bool neg) {
+    fx_add_signed(S.tor, t.hi, neg, S.flags);
+    fx_add_signed(S.tor, t.lo, neg, S.flags);
+    fx_add_signed(S.sabs, t.hi, false, S.flags);
+    fx_add_signed(S.sabs, t.lo, false, S.flags);
+  }
+};
+
+// ------------------------------------------------------ register subtrees
+template <class Tier, int R>
+struct RegNode;
+
+// child of size RP (modes after the pivot) computed from a parent accessor
+template <class Tier, int RP, class Get>
+__device__ __forceinline__ void reg_child(const Get &get, typename Tier::T a, typename Tier::T b,
+                                          typename Tier::T d, typename Tier::T y,
+                                          typename Tier::T tc, int parc, int k, Sums &S) {
+  using T = typename Tier::T;
+  T al, be, de;
+  Tier::coef(a, b, d, y, al, be, de);
+  T ux[2 * RP], up[2 * RP];
+#pragma unroll
+  for (int i = 0; i < 2 * RP; ++i) {
+    ux[i] = get(ix(2 * RP + 1, i));
+    up[i] = get(ix(2 * RP, i));
+  }
+  T C[sz(RP)];
+#pragma unroll
+  for (int i = 0; i < 2 * RP; ++i) {
+    T vx, vp;
+    Tier::vrow(al, be, de, ux[i], up[i], vx, vp);
+#pragma unroll
+    for (int j = 0; j <= i; ++j) C[ix(i, j)] = Tier::upd(get(ix(i, j)), vx, ux[j], vp, up[j]);
+  }
+  RegNode<Tier, RP>::visit(C, tc, parc, k, S);
+}
+
+template <class Tier, int R, int RP>
+struct RegChildren {
+  using T = typename Tier::T;
+  __device__ static __forceinline__ void run(const T (&M)[sz(R)], T t, int par, int k, Sums &S) {
+    const T a = M[ix(2 * RP + 1, 2 * RP + 1)], b = M[ix(2 * RP + 1, 2 * RP)], d = M[ix(2 * RP, 2 * RP)];
+    const T det2 = Tier::det2(a, b, d);
+    if (Tier::bad(det2)) S.flags |= ST_NOTPD;
+    const T y = Tier::rsqrt(det2);
+    const T tc = Tier::mul(t, y);
+    Tier::acc(S, tc, ((k ^ (par + 1)) & 1) != 0);
+    if constexpr (RP > 0) {
+      auto get = [&](int e) { return M[e]; };
+      reg_child<Tier, RP>(get, a, b, d, y, tc, par + 1, k, S);
+    }
+    RegChildren<Tier, R, RP + 1>::run(M, t, par, k, S);
+  }
+};
+template <class Tier, int R>
+struct RegChildren<Tier, R, R> {
+  using T = typename Tier::T;
+  __device__ static __forceinline__ void run(const T (&)[sz(R)], T, int, int, Sums &) {}
+};
+
+template <class Tier, int R>
+struct RegNode {
+  using T = typename Tier::T;
+  __device__ static __forceinline__ void visit(const T (&M)[sz(R)], T t, int par, int k, Sums &S) {
+    RegChildren<Tier, R, 0>::run(M, t, par, k, S);
+  }
+};
+
+// memory parent -> register child of size rp (1..RREG)
+template <class Tier>
+__device__ __forceinline__ void mem_to_reg_child(int rp, const double *P, size_t st,
+                                                 typename Tier::T a, typename Tier::T b,
+                                                 typename Tier::T d, typename Tier::T y,
+                                                 typename Tier::T tc, int parc, int k, Sums &S) {
+  auto get = [&](int e) { return Tier::ld(P, e, st); };
+  if constexpr (Tier::RREG >= 1) { if (rp == 1) { reg_child<Tier, 1>(get, a, b, d, y, tc, parc, k, S); return; } }
+  if constexpr (Tier::RREG >= 2) { if (rp == 2) { reg_child<Tier, 2>(get, a, b, d, y, tc, parc, k, S); return; } }
+  if constexpr (Tier::RREG >= 3) { if (rp == 3) { reg_child<Tier, 3>(get, a, b, d, y, tc, parc, k, S); return; } }
+  if constexpr (Tier::RREG >= 4) { if (rp == 4) { reg_child<Tier, 4>(get, a, b, d, y, tc, parc, k, S); return; } }
+}
+
+// ------------------------------------------------------- memory-tier update
+// child C (size rp) = parent P's trailing block minus the rank-2 term; C may equal P.
+template <class Tier>
+__device__ __forceinline__ void schur_mem(const double *P, double *C, size_t st, int rp,
+                                          typename Tier::T a, typename Tier::T b,
+                                          typename Tier::T d, typename Tier::T y) {
+  using T = typename Tier::T;
+  T al, be, de;
+  Tier::coef(a, b, d, y, al, be, de);
+  const int n2 = 2 * rp;
+  const int cx = ix(2 * rp + 1, 0), cp = ix(2 * rp, 0);
+  for (int i = 0; i < n2; ++i) {
+    const T uxi = Tier::ld(P, cx + i, st), upi = Tier::ld(P, cp + i, st);
+    T vx, vp;
+    Tier::vrow(al, be, de, uxi, upi, vx, vp);
+    const int row = ix(i, 0);
+#pragma unroll 2
+    for (int j = 0; j <= i; ++j) {
+      const T s = Tier::ld(P, row + j, st);
+      Tier::stv(C, row + j, st, Tier::upd(s, vx, Tier::ld(P, cx + j, st), vp, Tier::ld(P, cp + j, st)));
+    }
+  }
+}
+
+// per-thread stack extent (in entries) of a walk over r modes
+__host__ __device__ constexpr int stack_entries(int r, int rreg) {
+  int e = 0;
+  for (int j = r; j > rreg; j -= 2) e += sz(j);
+  return e;
+}
+
+// ------------------------------------------------------------ the walk
+// Visit every non-empty extension of the node stored at S (r modes, term t,
+// |Z| = par) in depth-first order; the node's own term is added by the caller.
+template <class Tier>
+__device__ void dfs_walk(double *S, size_t st, int r, typename Tier::T t, int par, int k, Sums &Sm) {
+  using T = typename Tier::T;
+  struct Frame { int off, r, rp, par; T t; };
+  Frame stk[33];
+  int sp = 0;
+  int off = 0, rp = 0;
+  while (true) {
+    if (rp < r) {
+      const int cur = rp++;
+      const double *P = S + (size_t)(off * Tier::W) * st;
+      const T a = Tier::ld(P, ix(2 * cur + 1, 2 * cur + 1), st);
+      const T b = Tier::ld(P, ix(2 * cur + 1, 2 * cur), st);
+      const T d = Tier::ld(P, ix(2 * cur, 2 * cur), st);
+      const T det2 = Tier::det2(a, b, d);
+      if (Tier::bad(det2)) Sm.flags |= ST_NOTPD;
+      const T y = Tier::rsqrt(det2);
+      const T tc = Tier::mul(t, y);
+      Tier::acc(Sm, tc, ((k ^ (par + 1)) & 1) != 0);
+      if (cur == 0) continue;
+      if (cur <= Tier::RREG) {
+        mem_to_reg_child<Tier>(cur, P, st, a, b, d, y, tc, par + 1, k, Sm);
+        continue;
+      }
+      if (cur == r - 1) {  // last child: in place, the node is finished afterwards
+        schur_mem<Tier>(P, const_cast<double *>(P), st, cur, a, b, d, y);
+        r = cur; rp = 0; t = tc; par = par + 1;
+        continue;
+      }
+      const int coff = off + sz(r);
+      schur_mem<Tier>(P, S + (size_t)(coff * Tier::W) * st, st, cur, a, b, d, y);
+      stk[sp++] = Frame{off, r, rp, par, t};
+      off = coff; r = cur; rp = 0; t = tc; par = par + 1;
+    } else {
+      if (sp == 0) break;
+      --sp;
+      off = stk[sp].off; r = stk[sp].r; rp = stk[sp].rp; par = stk[sp].par; t = stk[sp].t;
+    }
+  }
+}
+
+}  // namespace tor

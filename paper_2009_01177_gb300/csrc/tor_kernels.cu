@@ -1,0 +1,214 @@
+// tor_kernels.cu -- kernels of the Torontonian path (sm_103a).
+//
+//   k_prep        O (xxpp or xpxp, leading dim ld) -> B = I - O, mode-interleaved
+//                 2k x 2k (plus the exact low parts of the diagonal for the dd
+//                 tier).  Step a0: the selection of Eq. 1 is the caller's.
+//   k_dfs<Tier>   one thread per prefix chunk: chunk root + depth-first walk
+//                 (tor_dfs.cuh); exact fixed-point partials per block (and
+//                 per chunk on request).
+//   k_finalize    sums the block partials (exact) and writes a tor_result.
+//   k_dfma_peak   FP64 FMA throughput probe (the roofline denominator).
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "tor_dfs.cuh"
+#include "tor_internal.h"
+
+namespace tor {
+
+// B[(2i+q)*2k + (2j+q')] = delta - O[row(i,q)][row(j,q')];  Blo = exact low part of the diagonal
+__global__ void k_prep(const double *__restrict__ O, int k, int ld, int layout,
+                       double *__restrict__ B, double *__restrict__ Blo) {
+  const int n = 2 * k;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int r = idx / n, c = idx % n;
+  const int mi = r >> 1, qi = r & 1, mj = c >> 1, qj = c & 1;
+  const int ri = (layout == 0) ? (qi * k + mi) : r;
+  const int rj = (layout == 0) ? (qj * k + mj) : c;
+  const double o = O[(size_t)ri * ld + rj];
+  if (r == c) {
+    const dd s = two_sum(1.0, -o);  // 1 - o = s.hi + s.lo exactly
+    B[idx] = s.hi;
+    if (Blo) Blo[r] = s.lo;
+  } else {
+    B[idx] = -o;
+  }
+}
+
+template <class Tier>
+__device__ __forceinline__ typename Tier::T gather_entry(const double *__restrict__ B,
+                                                         const double *__restrict__ Blo, int n2k,
+                                                         int row, int col);
+template <>
+__device__ __forceinline__ double gather_entry<TierF64>(const double *__restrict__ B,
+                                                        const double *__restrict__, int n2k, int row,
+                                                        int col) {
+  return B[(size_t)row * n2k + col];
+}
+template <>
+__device__ __forceinline__ dd gather_entry<TierDD>(const double *__restrict__ B,
+                                                   const double *__restrict__ Blo, int n2k, int row,
+                                                   int col) {
+  return {B[(size_t)row * n2k + col], (row == col) ? Blo[row] : 0.0};
+}
+
+template <class Tier>
+__global__ void __launch_bounds__(128)
+k_dfs(const double *__restrict__ B, const double *__restrict__ Blo, int k, int r1,
+      unsigned long long c_begin, unsigned long long c_end, double *__restrict__ scratch,
+      unsigned long long *__restrict__ block_part, unsigned long long *__restrict__ chunk_part,
+      int *__restrict__ status) {
+  using T = typename Tier::T;
+  const size_t st = (size_t)gridDim.x * blockDim.x;
+  const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double *S = scratch + gtid;
+  const int n2k = 2 * k;
+
+  Fx256 tot_tor, tot_sabs;
+  fx_zero(tot_tor);
+  fx_zero(tot_sabs);
+  int flags = 0;
+  unsigned char pm[64];
+
+  for (unsigned long long c = c_begin + gtid; c < c_end; c += st) {
+    Sums Sm;
+    fx_zero(Sm.tor);
+    fx_zero(Sm.sabs);
+    Sm.flags = 0;
+    // chunk root: fixed modes r1 + j for the set bits j of c, then the low modes
+    int np = 0;
+    for (unsigned long long m = c; m; m &= m - 1) pm[np++] = (unsigned char)(r1 + __ffsll((long long)m) - 1);
+    const int n = np + r1;
+    for (int hi = 0; hi < 2 * n; ++hi) {
+      const int ph = n - 1 - (hi >> 1), qh = 1 - (hi & 1);
+      const int mh = (ph < np) ? pm[ph] : (ph - np);
+      for (int lo = 0; lo <= hi; ++lo) {
+        const int pl = n - 1 - (lo >> 1), ql = 1 - (lo & 1);
+        const int ml = (pl < np) ? pm[pl] : (pl - np);
+        Tier::stv(S, ix(hi, lo), st, gather_entry<Tier>(B, Blo, n2k, 2 * mh + qh, 2 * ml + ql));
+      }
+    }
+    T t = Tier::one();
+    for (int s = 0; s < np; ++s) {
+      const int rp = n - 1 - s;
+      const T a = Tier::ld(S, ix(2 * rp + 1, 2 * rp + 1), st);
+      const T b = Tier::ld(S, ix(2 * rp + 1, 2 * rp), st);
+      const T d = Tier::ld(S, ix(2 * rp, 2 * rp), st);
+      const T det2 = Tier::det2(a, b, d);
+      if (Tier::bad(det2)) Sm.flags |= ST_NOTPD;
+      const T y = Tier::rsqrt(det2);
+      t = Tier::mul(t, y);
+      if (rp > 0) schur_mem<Tier>(S, S, st, rp, a, b, d, y);
+    }
+    Tier::acc(Sm, t, ((k ^ np) & 1) != 0);
+    dfs_walk<Tier>(S, st, r1, t, np, k, Sm);
+
+    if (chunk_part) {
+      unsigned long long *o = chunk_part + (size_t)(c - c_begin) * 8;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) { o[i] = Sm.tor.w[i]; o[4 + i] = Sm.sabs.w[i]; }
+    }
+    fx_add(tot_tor, Sm.tor);
+    fx_add(tot_sabs, Sm.sabs);
+    flags |= Sm.flags;
+  }
+
+  // block reduction (exact, so the order does not matter)
+  __shared__ unsigned long long red[128][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) { red[threadIdx.x][i] = tot_tor.w[i]; red[threadIdx.x][4 + i] = tot_sabs.w[i]; }
+  if (flags) atomicOr(status, flags);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Fx256 a, b, x;
+    fx_zero(a);
+    fx_zero(b);
+    for (int t2 = 0; t2 < (int)blockDim.x; ++t2) {
+      for (int i = 0; i < 4; ++i) x.w[i] = red[t2][i];
+      fx_add(a, x);
+      for (int i = 0; i < 4; ++i) x.w[i] = red[t2][4 + i];
+      fx_add(b, x);
+    }
+    for (int i = 0; i < 4; ++i) {
+      block_part[(size_t)blockIdx.x * 8 + i] = a.w[i];
+      block_part[(size_t)blockIdx.x * 8 + 4 + i] = b.w[i];
+    }
+  }
+}
+
+__host__ __device__ void fixed_to_result(const unsigned long long *w8, int k, int tier, int status,
+                                         tor_result *out) {
+  Fx256 a, b;
+  for (int i = 0; i < 4; ++i) { a.w[i] = w8[i]; b.w[i] = w8[4 + i]; }
+  double hi, lo;
+  fx_to_dd(a, hi, lo);
+  out->hi = hi;
+  out->lo = lo;
+  out->sum_abs = fx_to_double(b);
+  out->err_est = err_gamma(k) * unit_roundoff(tier) * out->sum_abs;
+  out->tier = tier;
+  out->status = (status & ST_NOTPD) ? TOR_ENOTPD : ((status & ST_RANGE) ? TOR_EINVAL : TOR_OK);
+}
+
+__global__ void k_finalize(const unsigned long long *__restrict__ block_part, int nblocks, int k,
+                           int tier, const int *__restrict__ status, tor_result *__restrict__ out,
+                           unsigned long long *__restrict__ total8) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Fx256 a, b, x;
+  fx_zero(a);
+  fx_zero(b);
+  for (int j = 0; j < nblocks; ++j) {
+    for (int i = 0; i < 4; ++i) x.w[i] = block_part[(size_t)j * 8 + i];
+    fx_add(a, x);
+    for (int i = 0; i < 4; ++i) x.w[i] = block_part[(size_t)j * 8 + 4 + i];
+    fx_add(b, x);
+  }
+  unsigned long long w8[8];
+  for (int i = 0; i < 4; ++i) { w8[i] = a.w[i]; w8[4 + i] = b.w[i]; }
+  if (total8) for (int i = 0; i < 8; ++i) total8[i] = w8[i];
+  fixed_to_result(w8, k, tier, *status, out);
+}
+
+// Independent DFMA chains; the result is consumed so the loop is not removed.
+__global__ void k_dfma_peak(double *sink, int iters, double a, double b) {
+  double x0 = threadIdx.x * 1e-9, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3;
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+  }
+  const double s = x0 + x1 + x2 + x3;
+  if (s == 1234.5) sink[threadIdx.x] = s;
+}
+
+// ------------------------------------------------------------ host launchers
+void launch_prep(const double *O, int k, int ld, int layout, double *B, double *Blo, cudaStream_t s) {
+  const int n = 4 * k * k;
+  k_prep<<<(n + 255) / 256, 256, 0, s>>>(O, k, ld, layout, B, Blo);
+}
+
+void launch_dfs(int tier, int grid, int block, const double *B, const double *Blo, int k, int r1,
+                unsigned long long c0, unsigned long long c1, double *scratch,
+                unsigned long long *block_part, unsigned long long *chunk_part, int *status,
+                cudaStream_t s) {
+  if (tier == TOR_PREC_DD)
+    k_dfs<TierDD><<<grid, block, 0, s>>>(B, Blo, k, r1, c0, c1, scratch, block_part, chunk_part, status);
+  else
+    k_dfs<TierF64><<<grid, block, 0, s>>>(B, Blo, k, r1, c0, c1, scratch, block_part, chunk_part, status);
+}
+
+void launch_finalize(const unsigned long long *block_part, int nblocks, int k, int tier,
+                     const int *status, tor_result *out, unsigned long long *total8, cudaStream_t s) {
+  k_finalize<<<1, 32, 0, s>>>(block_part, nblocks, k, tier, status, out, total8);
+}
+
+void launch_dfma_peak(double *sink, int grid, int block, int iters, cudaStream_t s) {
+  k_dfma_peak<<<grid, block, 0, s>>>(sink, iters, 1.0000001, 1e-9);
+}
+
+int scratch_entries(int tier, int k, int r1) {
+  const int rreg = (tier == TOR_PREC_DD) ? TierDD::RREG : TierF64::RREG;
+  const int w = (tier == TOR_PREC_DD) ? 2 : 1;
+  const int a = sz(k), b = stack_entries(r1, rreg);
+  return w * (a > b ? a : b);
+}
+
+}  // namespace tor

@@ -1,0 +1,234 @@
+"""Python binding of the C ABI in include/torontonian.h (argument marshalling only).
+
+Every step of the Torontonian runs in the CUDA library libtorontonian.so; this
+module converts torch tensors to device pointers and streams, and results to
+Python objects.  There is no CPU fallback: if the library is missing or no
+GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtorontonian.so")
+
+TOR_OK, TOR_EINVAL, TOR_ENOTPD, TOR_ECUDA, TOR_ETIMEOUT, TOR_EPREC, TOR_ENOMEM = range(7)
+PREC_AUTO, PREC_FP64, PREC_DD = 0, 1, 2
+LAYOUT_XXPP, LAYOUT_XPXP = 0, 1
+_PREC = {"auto": PREC_AUTO, "fp64": PREC_FP64, "dd": PREC_DD}
+_LAYOUT = {"xxpp": LAYOUT_XXPP, "xpxp": LAYOUT_XPXP}
+
+
+class TorResultC(ctypes.Structure):
+    _fields_ = [("hi", ctypes.c_double), ("lo", ctypes.c_double), ("sum_abs", ctypes.c_double),
+                ("err_est", ctypes.c_double), ("tier", ctypes.c_int), ("status", ctypes.c_int)]
+
+
+class TorBoundC(ctypes.Structure):
+    _fields_ = [("log_tmax", ctypes.c_float), ("log_tor_est", ctypes.c_float),
+                ("log_kappa_est", ctypes.c_float), ("bits_needed", ctypes.c_float),
+                ("tier", ctypes.c_int)]
+
+
+RESULT_BYTES = ctypes.sizeof(TorResultC)
+BOUND_BYTES = ctypes.sizeof(TorBoundC)
+
+
+class TorError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+@dataclasses.dataclass
+class TorResult:
+    hi: float
+    lo: float
+    sum_abs: float
+    err_est: float
+    tier: int
+    status: int
+
+    @property
+    def value(self) -> float:
+        return self.hi + self.lo
+
+    @property
+    def kappa(self) -> float:
+        return self.sum_abs / abs(self.hi) if self.hi else float("inf")
+
+    @classmethod
+    def from_c(cls, r: TorResultC) -> "TorResult":
+        return cls(r.hi, r.lo, r.sum_abs, r.err_est, r.tier, r.status)
+
+    @classmethod
+    def from_bytes(cls, b: bytes) -> "TorResult":
+        return cls.from_c(TorResultC.from_buffer_copy(b))
+
+
+_lib = None
+_lock = threading.Lock()
+
+# name -> (restype, argtypes); the same names as include/torontonian.h
+_VP, _I, _D, _U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint64
+SIGNATURES = {
+    "tor_create": (_I, [ctypes.POINTER(_VP), _I]),
+    "tor_destroy": (None, [_VP]),
+    "tor_last_error": (ctypes.c_char_p, []),
+    "tor_set_launch": (_I, [_VP, _I, _I]),
+    "tor_set_chunk_bits": (_I, [_VP, _I]),
+    "tor_single": (_I, [_VP, _VP, _I, _I, _I, _I, _D, _VP, ctypes.POINTER(TorResultC)]),
+    "tor_single_async": (_I, [_VP, _VP, _I, _I, _I, _I, _VP, _VP]),
+    "tor_chunks": (_I, [_VP, _VP, _I, _I, _I, _I, _I, _U64, _U64, _VP, _VP]),
+    "tor_fixed_to_result": (_I, [ctypes.POINTER(_U64), _I, _I, ctypes.POINTER(TorResultC)]),
+    "tor_batch": (_I, [_VP, _VP, _VP, _VP, _I, _I, _I, _D, _VP, _VP]),
+    "tor_bounds": (_I, [_VP, _VP, _VP, _VP, _I, _I, _D, _VP, _VP]),
+    "tor_fp64_peak": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "tor_set_timing": (_I, [_VP, _I]),
+    "tor_walk_time": (_I, [_VP, ctypes.POINTER(ctypes.c_float)]),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtorontonian.so and declare every exported entry point."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it first "
+                                   "(python -c 'import __graft_entry__ as g; g.build()')")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int):
+    if rc != TOR_OK:
+        raise TorError(rc, load_library().tor_last_error().decode())
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _mat(O: torch.Tensor):
+    if not (isinstance(O, torch.Tensor) and O.is_cuda and O.dtype == torch.float64 and O.dim() == 2):
+        raise ValueError("O must be a 2-D float64 CUDA tensor")
+    if O.shape[0] != O.shape[1] or O.shape[0] % 2:
+        raise ValueError("O must be 2k x 2k")
+    if O.stride(1) != 1:
+        raise ValueError("O must be row-major (unit column stride)")
+    return O.shape[0] // 2, O.stride(0)
+
+
+class Context:
+    """A library context on one CUDA device (workspace, launch settings)."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load_library()
+        self.device = device
+        h = ctypes.c_void_p()
+        _check(self.lib.tor_create(ctypes.byref(h), device))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tor_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_launch(self, threads_per_block: int = 0, blocks_per_sm: int = 0):
+        _check(self.lib.tor_set_launch(self.h, threads_per_block, blocks_per_sm))
+
+    def set_chunk_bits(self, d: int):
+        _check(self.lib.tor_set_chunk_bits(self.h, d))
+
+    def single(self, O: torch.Tensor, prec: str = "fp64", layout: str = "xxpp", tol: float = 1e-10,
+               stream=None) -> TorResult:
+        """Tor(O) of one 2k x 2k matrix (blocking)."""
+        k, ld = _mat(O)
+        out = TorResultC()
+        _check(self.lib.tor_single(self.h, O.data_ptr(), k, ld, _LAYOUT[layout], _PREC[prec], tol,
+                                   _stream(stream), ctypes.byref(out)))
+        return TorResult.from_c(out)
+
+    def single_async(self, O: torch.Tensor, out: torch.Tensor, prec: str = "fp64",
+                     layout: str = "xxpp", stream=None):
+        """Enqueue Tor(O); the raw tor_result lands in the uint8 CUDA tensor `out`."""
+        k, ld = _mat(O)
+        if out.dtype != torch.uint8 or out.numel() < RESULT_BYTES or not out.is_cuda:
+            raise ValueError(f"out must be a uint8 CUDA tensor of >= {RESULT_BYTES} bytes")
+        _check(self.lib.tor_single_async(self.h, O.data_ptr(), k, ld, _LAYOUT[layout], _PREC[prec],
+                                         _stream(stream), out.data_ptr()))
+
+    def chunks(self, O: torch.Tensor, chunk_bits: int, c_begin: int, c_end: int, prec: str = "fp64",
+               layout: str = "xxpp", stream=None) -> torch.Tensor:
+        """Exact per-chunk partials, an int64 CUDA tensor (c_end - c_begin, 8) of raw limbs."""
+        k, ld = _mat(O)
+        part = torch.zeros((max(c_end - c_begin, 0), 8), dtype=torch.int64, device=O.device)
+        _check(self.lib.tor_chunks(self.h, O.data_ptr(), k, ld, _LAYOUT[layout], _PREC[prec],
+                                   chunk_bits, c_begin, c_end, _stream(stream), part.data_ptr()))
+        return part
+
+    def set_timing(self, on: bool):
+        _check(self.lib.tor_set_timing(self.h, int(bool(on))))
+
+    def walk_time_ms(self) -> float:
+        ms = ctypes.c_float()
+        _check(self.lib.tor_walk_time(self.h, ctypes.byref(ms)))
+        return ms.value
+
+    def fp64_peak(self):
+        """(measured DFMA per second, nominal SM clock in Hz)."""
+        r, c = ctypes.c_double(), ctypes.c_double()
+        _check(self.lib.tor_fp64_peak(self.h, ctypes.byref(r), ctypes.byref(c)))
+        return r.value, c.value
+
+
+def fixed_to_result(limbs8, k: int, tier: str = "fp64") -> TorResult:
+    """Convert 8 raw limbs (signed sum, sum_abs; 256-bit fixed point, 128 fraction bits)."""
+    arr = (ctypes.c_uint64 * 8)(*[int(x) & 0xFFFFFFFFFFFFFFFF for x in limbs8])
+    out = TorResultC()
+    _check(load_library().tor_fixed_to_result(arr, k, _PREC[tier], ctypes.byref(out)))
+    return TorResult.from_c(out)
+
+
+def limbs_to_int(limbs4) -> int:
+    """Signed Python integer of 4 little-endian 64-bit limbs (value = int / 2^128)."""
+    v = 0
+    for i, x in enumerate(limbs4):
+        v |= (int(x) & 0xFFFFFFFFFFFFFFFF) << (64 * i)
+    if v >> 255:
+        v -= 1 << 256
+    return v
+
+
+_default = None
+
+
+def default_context(device: int = 0) -> Context:
+    global _default
+    if _default is None:
+        _default = Context(device)
+    return _default
+
+
+def tor_single(O: torch.Tensor, prec: str = "fp64", layout: str = "xxpp", tol: float = 1e-10,
+               stream=None) -> TorResult:
+    return default_context(O.device.index or 0).single(O, prec=prec, layout=layout, tol=tol, stream=stream)

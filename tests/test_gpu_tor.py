@@ -1,0 +1,207 @@
+"""GPU parity tests: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances.  Each term t_Z is computed in the tier's arithmetic and summed
+exactly, so the error of a result is bounded by gamma * u * sum_Z t_Z with
+gamma = 4k, u = 2^-53 (FP64) or 2^-104 (double-double): every test asserts
+|GPU - oracle| <= err_est.  Where the instance's condition number allows it,
+tests also assert the relative targets 1e-10 (FP64) and 1e-20 (dd).
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2009_01177_gb300 import gbs_inputs as gi
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(O):
+    return torch.from_numpy(np.ascontiguousarray(O)).to("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def ctx(cuda_lib):
+    c = cuda_lib.Context(0)
+    yield c
+    c.close()
+
+
+def err_vs(r, ref):
+    return abs(float(Fraction(r.hi) + Fraction(r.lo) - Fraction(ref.hi) - Fraction(ref.lo)))
+
+
+TARGET = {"fp64": 1e-10, "dd": 1e-20}
+
+
+def check(r, ref, prec):
+    """|err| within the a-posteriori bound always; the relative target where kappa allows it."""
+    e = err_vs(r, ref)
+    assert r.status == 0
+    assert e <= r.err_est, (e, r.err_est)
+    if r.err_est <= TARGET[prec] * abs(ref.value):
+        assert e <= TARGET[prec] * abs(ref.value), (e / abs(ref.value), ref.kappa)
+    return e
+
+
+def test_empty_pattern(ctx):
+    r = ctx.single(torch.zeros((0, 0), dtype=torch.float64, device="cuda:0"))
+    assert (r.hi, r.lo, r.status) == (1.0, 0.0, 0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "dd"])
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 8, 11, 13])
+def test_thermal_closed_form(ctx, prec, k):
+    # O = a I: Tor = (a/(1-a))^k exactly; kappa = ((2-a)/a)^k = 7^k at a = 1/4
+    a = 0.25
+    r = ctx.single(dev(gi.thermal_O(k, a)), prec=prec)
+    exact = Fraction(1, 3) ** k
+    got = Fraction(r.hi) + Fraction(r.lo)
+    assert abs(float(got - exact)) <= r.err_est
+    target = 1e-10 if prec == "fp64" else 1e-20
+    if r.err_est <= target * float(exact):          # the conditioning allows the relative target
+        assert abs(float((got - exact) / exact)) <= target
+
+
+@pytest.mark.parametrize("prec", ["fp64", "dd"])
+def test_m16_k10_against_oracle(ctx, prec):
+    st, pat, O = gi.workload_m16_k10()
+    ref = oracle.tor(O)
+    r = ctx.single(dev(O), prec=prec)
+    check(r, ref, prec)
+    assert abs(r.sum_abs - ref.sum_abs) <= 1e-12 * ref.sum_abs
+    if prec == "dd":                       # kappa = 1.7e8 leaves dd well inside 1e-20
+        assert err_vs(r, ref) <= 1e-20 * abs(ref.value)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "dd"])
+@pytest.mark.parametrize("k", [12, 14, 16])
+def test_m100_nested_patterns_against_oracle(ctx, prec, k):
+    st, pat, O32 = gi.workload_m100(32)
+    O = gi.select(st.O, pat[:k])
+    ref = oracle.tor(O)
+    r = ctx.single(dev(O), prec=prec)
+    check(r, ref, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "dd"])
+def test_well_conditioned_meets_relative_targets(ctx, prec):
+    # bright modes: click probabilities near 1 make the sum well conditioned
+    st = gi.lossy_gbs_state(24, 1.6, 2.0, 0.9, 77)
+    O = gi.select(st.O, gi.random_pattern(24, 14, 77))
+    ref = oracle.tor(O)
+    r = ctx.single(dev(O), prec=prec)
+    rel = err_vs(r, ref) / abs(ref.value)
+    assert rel <= (1e-10 if prec == "fp64" else 1e-20), (rel, ref.kappa)
+
+
+def test_chunk_partials_match_oracle_ranges(ctx):
+    st, pat, O32 = gi.workload_m100(32)
+    O = gi.select(st.O, pat[:14])
+    k, d = 14, 5
+    part = ctx.chunks(dev(O), d, 0, 1 << d).cpu().numpy()
+    from paper_2009_01177_gb300.tor import limbs_to_int
+    for c in [0, 1, 7, 19, 31]:
+        ref = oracle.tor_range(O, c << (k - d), (c + 1) << (k - d))
+        got = Fraction(limbs_to_int(part[c, :4]), 1 << 128)
+        sabs = Fraction(limbs_to_int(part[c, 4:]), 1 << 128)
+        assert abs(float(sabs) - ref.sum_abs) <= 1e-13 * ref.sum_abs
+        assert abs(float(got - Fraction(ref.hi) - Fraction(ref.lo))) <= 4 * k * 2.0 ** -53 * ref.sum_abs
+
+
+def test_sharded_chunks_add_up_exactly(ctx):
+    st, pat, O32 = gi.workload_m100(32)
+    O = gi.select(st.O, pat[:18])
+    Od = dev(O)
+    d = 8
+    whole = ctx.chunks(Od, d, 0, 1 << d).cpu().numpy()
+    a = ctx.chunks(Od, d, 0, 100).cpu().numpy()
+    b = ctx.chunks(Od, d, 100, 1 << d).cpu().numpy()
+    assert np.array_equal(np.concatenate([a, b]), whole)        # chunks are independent
+    from paper_2009_01177_gb300.tor import limbs_to_int, fixed_to_result
+    tot = [sum(limbs_to_int(whole[c, 4 * h:4 * h + 4]) for c in range(1 << d)) for h in (0, 1)]
+    limbs = []
+    for v in tot:
+        v &= (1 << 256) - 1
+        limbs += [(v >> (64 * i)) & 0xFFFFFFFFFFFFFFFF for i in range(4)]
+    r_sh = fixed_to_result(limbs, 18)
+    ctx.set_chunk_bits(d)
+    r = ctx.single(Od)
+    ctx.set_chunk_bits(-1)
+    assert (r_sh.hi, r_sh.lo) == (r.hi, r.lo)
+
+
+def test_launch_shape_does_not_change_bits(ctx):
+    st, pat, O = gi.workload_m16_k10()
+    O = gi.select(st.O, gi.random_pattern(16, 15, 3))
+    Od = dev(O)
+    base = ctx.single(Od)
+    for tpb, bps in [(32, 1), (64, 3), (128, 1)]:
+        ctx.set_launch(tpb, bps)
+        r = ctx.single(Od)
+        assert (r.hi, r.lo, r.sum_abs) == (base.hi, base.lo, base.sum_abs)
+    ctx.set_launch(0, 0)
+
+
+def test_chunk_depth_changes_only_rounding(ctx):
+    st, pat, O32 = gi.workload_m100(32)
+    O = gi.select(st.O, pat[:16])
+    ref = oracle.tor(O)
+    Od = dev(O)
+    for d in [0, 3, 8, 16]:
+        ctx.set_chunk_bits(d)
+        r = ctx.single(Od)
+        assert err_vs(r, ref) <= r.err_est, d
+    ctx.set_chunk_bits(-1)
+
+
+def test_layouts_agree(ctx):
+    st, pat, O = gi.workload_m16_k10()
+    k = O.shape[0] // 2
+    perm = np.empty(2 * k, dtype=int)
+    perm[0::2] = np.arange(k)
+    perm[1::2] = k + np.arange(k)
+    Oi = O[np.ix_(perm, perm)]
+    a = ctx.single(dev(O), layout="xxpp")
+    b = ctx.single(dev(Oi), layout="xpxp")
+    assert (a.hi, a.lo) == (b.hi, b.lo)
+
+
+def test_leading_dimension(ctx):
+    st, pat, O = gi.workload_m16_k10()
+    big = np.zeros((O.shape[0], O.shape[1] + 7))
+    big[:, :O.shape[1]] = O
+    a = ctx.single(dev(O))
+    b = ctx.single(dev(big)[:, :O.shape[1]])
+    assert (a.hi, a.lo) == (b.hi, b.lo)
+
+
+def test_not_positive_definite_is_reported(ctx, cuda_lib):
+    O = 2.0 * np.eye(8)   # B = I - O = -I
+    with pytest.raises(cuda_lib.TorError) as ei:
+        ctx.single(dev(O))
+    assert ei.value.code == cuda_lib.TOR_ENOTPD
+
+
+def test_invalid_arguments(ctx, cuda_lib):
+    with pytest.raises(cuda_lib.TorError):
+        ctx.set_launch(48, 1)
+    with pytest.raises(cuda_lib.TorError):
+        ctx.chunks(dev(np.zeros((8, 8))), 5, 0, 1)   # chunk_bits > k
+
+
+@pytest.mark.slow
+def test_k32_block_factorisation(ctx):
+    # full-size check: Tor(O1 (+) O2) = Tor(O1) Tor(O2) with 16 + 16 modes of the M = 100 state
+    st, pat, O32 = gi.workload_m100(32)
+    O1 = gi.select(st.O, pat[:16])
+    O2 = gi.select(st.O, pat[16:])
+    r1, r2 = oracle.tor(O1), oracle.tor(O2)
+    prod = (Fraction(r1.hi) + Fraction(r1.lo)) * (Fraction(r2.hi) + Fraction(r2.lo))
+    r = ctx.single(dev(gi.block_diag_modes(O1, O2)), prec="fp64")
+    got = Fraction(r.hi) + Fraction(r.lo)
+    assert abs(float(got - prod)) <= r.err_est
+    sabs = r1.sum_abs * r2.sum_abs
+    assert abs(r.sum_abs - sabs) <= 1e-12 * sabs
