@@ -38,7 +38,7 @@ struct tor_ctx {
   int device = 0;
   int sms = 0;
   int threads_per_block = 128;
-  int blocks_per_sm = 2;
+  int blocks_per_sm = 4;  // clamped to the kernel's occupancy at launch
   int chunk_bits = -1;  // -1: automatic
   Buf B, Blo, scratch, block_part, status, result, total8;
   bool timing = false, timed = false;
@@ -90,7 +90,10 @@ int enqueue_walk(tor_ctx *ctx, const double *O, int k, int ld, int layout, int t
                  cudaStream_t s, int *grid_out) {
   const int r1 = k - d;
   const int block = ctx->threads_per_block;
-  const int grid = ctx->sms * ctx->blocks_per_sm;
+  // every block of the grid must be resident at once: chunks are dealt out by
+  // a grid stride, so a block that waited for a free SM would double the time
+  const int occ = tor::dfs_max_blocks_per_sm(tier, block);
+  const int grid = ctx->sms * (ctx->blocks_per_sm < occ ? ctx->blocks_per_sm : occ);
   const size_t nthreads = (size_t)grid * block;
   int rc;
   if ((rc = ensure(ctx, ctx->B, sizeof(double) * 4 * (size_t)k * k))) return rc;
@@ -179,7 +182,7 @@ int tor_walk_time(tor_ctx *ctx, float *ms) {
 int tor_set_launch(tor_ctx *ctx, int threads_per_block, int blocks_per_sm) {
   if (!ctx) return fail(TOR_EINVAL, "null context");
   if (threads_per_block == 0) threads_per_block = 128;
-  if (blocks_per_sm == 0) blocks_per_sm = 2;
+  if (blocks_per_sm == 0) blocks_per_sm = 4;
   if (threads_per_block != 32 && threads_per_block != 64 && threads_per_block != 128)
     return fail(TOR_EINVAL, "threads_per_block must be 32, 64 or 128");
   if (blocks_per_sm < 1 || blocks_per_sm > 16) return fail(TOR_EINVAL, "blocks_per_sm outside [1, 16]");

@@ -75,25 +75,56 @@ __device__ __forceinline__ void fx_add_signed(Fx256 &acc, double x, bool neg, in
   if (neg != xneg) fx_sub(acc, X); else fx_add(acc, X);
 }
 
-// ------------------------------------------------------------ FP64 tier
-struct TierF64 {
-  using T = double;
-  static constexpr int W = 1;      // doubles per stored entry
-  static constexpr int RREG = 3;   // register-resident subtree size (modes)
+// ------------------------------------------------------- FP64 primitives
+// Tuning switches (compile time).  Defaults are the fastest measured on GB300
+// for the k = 32 workload: larger register subtrees, unrolled memory-tier
+// updates and the FP32-seeded reciprocal square root all shorten the FP64
+// instruction count but lengthen dependency chains or code, and the walk is
+// latency-bound rather than FP64-issue-bound.
+#ifndef TOR_F64_RREG
+#define TOR_F64_RREG 3
+#endif
+#ifndef TOR_F64_RUNROLL
+#define TOR_F64_RUNROLL 0
+#endif
+#ifndef TOR_RSQRT_DF
+#define TOR_RSQRT_DF 0
+#endif
 
-  __device__ static __forceinline__ T ld(const double *P, int e, size_t st) { return P[(size_t)e * st]; }
-  __device__ static __forceinline__ void stv(double *P, int e, size_t st, T v) { P[(size_t)e * st] = v; }
-  __device__ static __forceinline__ T one() { return 1.0; }
-  __device__ static __forceinline__ T det2(T a, T b, T d) { return fma(a, d, -(b * b)); }
-  // not (0 < x < inf): integer test on the bit pattern, no FP64 compare
-  __device__ static __forceinline__ bool bad(T x) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-    return (u - 1ull) >= 0x7FEFFFFFFFFFFFFFull;
-  }
-  // 1/sqrt(x): FP32 seed (22.9 bits), two Newton steps y <- y + y(1/2 - (x/2) y^2) in FP64
-  __device__ static __forceinline__ T rsqrt(T x) {
+__device__ __forceinline__ double dmul(double a, double b) { return a * b; }
+
+// 1/sqrt(x) for a positive double x, accurate to about one ulp.
+// Default: FP32 seed (22.9 bits) and two FP64 Newton steps
+// y <- y + y (1/2 - (x/2) y^2).  With TOR_RSQRT_DF, the seed comes instead
+// from a double-float step: x is split EXACTLY into two floats by integer operations on its bit
+// pattern, x = xh + xl (xh = the top 24 mantissa bits); one Newton step
+// y1 = y0 + y0 e / 2, e = 1 - x y0^2, is taken in FP32 arithmetic with the
+// products kept exact by FMA (TwoProd), giving ~45 correct bits as y0 + c.
+// Then one FP64 Newton step y <- y + y (1/2 - (x/2) y^2) doubles that past
+// 53 bits.  FP64 pipe cost: one add and three FMA-type operations, against
+// six for two FP64 Newton steps from a 23-bit seed.  Inputs outside
+// [2^-74, 2^100) take two FP64 Newton steps from the FP64 approximation.
+__device__ __forceinline__ double rsqrt_fp64(double x) {
+  const long long bx = __double_as_longlong(x);
+  const int ex = (int)(bx >> 52);  // biased exponent, x > 0
+  const double hx = __longlong_as_double(bx - (1ll << 52));  // x / 2, exact for normal x
+  double y;
+  if (TOR_RSQRT_DF && ex >= 949 && ex < 1123) {  // x in [2^-74, 2^100): both halves are normal floats
+    const unsigned long long m = ((unsigned long long)bx & 0xFFFFFFFFFFFFFull);  // 52 fraction bits
+    const float xh = __int_as_float(((ex - 1023 + 127) << 23) | (int)(m >> 29));
+    const float xl = __uint2float_rn((unsigned)(m & 0x1FFFFFFFull)) *
+                     __int_as_float((ex - 1075 + 127) << 23);
+    float y0;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(xh));
+    const float ph = y0 * y0, pl = fmaf(y0, y0, -ph);      // y0^2 = ph + pl exactly
+    const float q = xh * ph, ql = fmaf(xh, ph, -q);        // xh ph = q + ql exactly
+    const float e = (1.0f - q) - (ql + fmaf(xh, pl, xl * ph));
+    const float c = (0.5f * y0) * e;
+    y = (double)y0 + (double)c;
+    const double r = fma(-dmul(hx, y), y, 0.5);
+    y = fma(y, r, y);
+  } else {  // 23-bit FP32 seed (or the FP64 approximation out of float range), two FP64 steps
     const float xf = __double2float_rn(x);
-    double y;
     if (xf > 1e-30f && xf < 1e30f) {
       float yf;
       asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
@@ -101,24 +132,41 @@ struct TierF64 {
     } else {
       asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
     }
-    // x/2 by an exponent decrement (integer pipe); x is a positive normal here
-    const double hx = __longlong_as_double(__double_as_longlong(x) - (1ll << 52));
-    double e = fma(-(hx * y), y, 0.5);
-    y = fma(y, e, y);
-    e = fma(-(hx * y), y, 0.5);
-    y = fma(y, e, y);
-    return y;
+    double r = fma(-dmul(hx, y), y, 0.5);
+    y = fma(y, r, y);
+    r = fma(-dmul(hx, y), y, 0.5);
+    y = fma(y, r, y);
   }
-  __device__ static __forceinline__ T mul(T a, T b) { return a * b; }
+  return y;
+}
+
+// ------------------------------------------------------------ FP64 tier
+struct TierF64 {
+  using T = double;
+  static constexpr int W = 1;      // doubles per stored entry
+  static constexpr int RREG = TOR_F64_RREG;       // register-resident subtree size (modes)
+  static constexpr int RUNROLL = TOR_F64_RUNROLL; // memory-tier updates unrolled up to this child size
+
+  __device__ static __forceinline__ T ld(const double *P, int e, size_t st) { return P[(size_t)e * st]; }
+  __device__ static __forceinline__ void stv(double *P, int e, size_t st, T v) { P[(size_t)e * st] = v; }
+  __device__ static __forceinline__ T one() { return 1.0; }
+  __device__ static __forceinline__ T det2(T a, T b, T d) { return fma(a, d, -dmul(b, b)); }
+  // not (0 < x < inf): integer test on the bit pattern, no FP64 compare
+  __device__ static __forceinline__ bool bad(T x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    return (u - 1ull) >= 0x7FEFFFFFFFFFFFFFull;
+  }
+  __device__ static __forceinline__ T rsqrt(T x) { return rsqrt_fp64(x); }
+  __device__ static __forceinline__ T mul(T a, T b) { return dmul(a, b); }
   // pivot coefficients: S_cc^-1 = [[al, -be], [-be, de]] with inv = y^2 = 1/det2
   __device__ static __forceinline__ void coef(T a, T b, T d, T y, T &al, T &be, T &de) {
-    const T inv = y * y;
-    al = d * inv; be = b * inv; de = a * inv;
+    const T inv = dmul(y, y);
+    al = dmul(d, inv); be = dmul(b, inv); de = dmul(a, inv);
   }
   // v = S_cc^-1 u
   __device__ static __forceinline__ void vrow(T al, T be, T de, T ux, T up, T &vx, T &vp) {
-    vx = fma(al, ux, -(be * up));
-    vp = fma(de, up, -(be * ux));
+    vx = fma(al, ux, -dmul(be, up));
+    vp = fma(de, up, -dmul(be, ux));
   }
   __device__ static __forceinline__ T upd(T s, T vx, T ux, T vp, T up) {
     return fma(-vp, up, fma(-vx, ux, s));
@@ -134,6 +182,7 @@ struct TierDD {
   using T = dd;
   static constexpr int W = 2;
   static constexpr int RREG = 2;
+  static constexpr int RUNROLL = 4;
 
   __device__ static __forceinline__ T ld(const double *P, int e, size_t st) {
     return {P[(size_t)(2 * e) * st], P[(size_t)(2 * e + 1) * st]};
@@ -201,7 +250,7 @@ struct RegChildren {
   __device__ static __forceinline__ void run(const T (&M)[sz(R)], T t, int par, int k, Sums &S) {
     const T a = M[ix(2 * RP + 1, 2 * RP + 1)], b = M[ix(2 * RP + 1, 2 * RP)], d = M[ix(2 * RP, 2 * RP)];
     const T det2 = Tier::det2(a, b, d);
-    if (Tier::bad(det2)) S.flags |= ST_NOTPD;
+    if (Tier::bad(det2) || Tier::bad(a)) S.flags |= ST_NOTPD;  // 2x2 block PD iff a > 0 and det > 0
     const T y = Tier::rsqrt(det2);
     const T tc = Tier::mul(t, y);
     Tier::acc(S, tc, ((k ^ (par + 1)) & 1) != 0);
@@ -241,10 +290,11 @@ __device__ __forceinline__ void mem_to_reg_child(int rp, const double *P, size_t
 
 // ------------------------------------------------------- memory-tier update
 // child C (size rp) = parent P's trailing block minus the rank-2 term; C may equal P.
+// Looped form, for children larger than Tier::RUNROLL modes (rare).
 template <class Tier>
-__device__ __forceinline__ void schur_mem(const double *P, double *C, size_t st, int rp,
-                                          typename Tier::T a, typename Tier::T b,
-                                          typename Tier::T d, typename Tier::T y) {
+__device__ __noinline__ void schur_mem_loop(const double *P, double *C, size_t st, int rp,
+                                            typename Tier::T a, typename Tier::T b,
+                                            typename Tier::T d, typename Tier::T y) {
   using T = typename Tier::T;
   T al, be, de;
   Tier::coef(a, b, d, y, al, be, de);
@@ -255,12 +305,61 @@ __device__ __forceinline__ void schur_mem(const double *P, double *C, size_t st,
     T vx, vp;
     Tier::vrow(al, be, de, uxi, upi, vx, vp);
     const int row = ix(i, 0);
-#pragma unroll 2
+#pragma unroll 4
     for (int j = 0; j <= i; ++j) {
       const T s = Tier::ld(P, row + j, st);
       Tier::stv(C, row + j, st, Tier::upd(s, vx, Tier::ld(P, cx + j, st), vp, Tier::ld(P, cp + j, st)));
     }
   }
+}
+
+// Unrolled form for a compile-time child size RP: the pivot columns stay in
+// registers, so each child entry costs one load and one store.  P and C may
+// be the same storage (the in-place last child); every entry is read before it
+// is written and never read again, so no reordering of independent accesses
+// can change the result, which is what the restrict qualifiers allow.
+template <class Tier, int RP>
+__device__ __forceinline__ void schur_mem_fixed(const double *__restrict__ P, double *__restrict__ C,
+                                                size_t st, typename Tier::T a, typename Tier::T b,
+                                                typename Tier::T d, typename Tier::T y) {
+  using T = typename Tier::T;
+  T al, be, de;
+  Tier::coef(a, b, d, y, al, be, de);
+  T ux[2 * RP], up[2 * RP];
+#pragma unroll
+  for (int i = 0; i < 2 * RP; ++i) {
+    ux[i] = Tier::ld(P, ix(2 * RP + 1, i), st);
+    up[i] = Tier::ld(P, ix(2 * RP, i), st);
+  }
+#pragma unroll
+  for (int i = 0; i < 2 * RP; ++i) {
+    T vx, vp;
+    Tier::vrow(al, be, de, ux[i], up[i], vx, vp);
+#pragma unroll
+    for (int j = 0; j <= i; ++j)
+      Tier::stv(C, ix(i, j), st, Tier::upd(Tier::ld(P, ix(i, j), st), vx, ux[j], vp, up[j]));
+  }
+}
+
+template <class Tier, int RP>
+__device__ __forceinline__ bool schur_try(int rp, const double *P, double *C, size_t st,
+                                          typename Tier::T a, typename Tier::T b,
+                                          typename Tier::T d, typename Tier::T y) {
+  if constexpr (RP > Tier::RUNROLL) {
+    return false;
+  } else {
+    if (rp == RP) { schur_mem_fixed<Tier, RP>(P, C, st, a, b, d, y); return true; }
+    return schur_try<Tier, RP + 1>(rp, P, C, st, a, b, d, y);
+  }
+}
+
+// one out-of-line copy of the dispatch, so the unrolled bodies exist once in
+// the binary however many call sites there are (instruction-cache footprint)
+template <class Tier>
+__device__ __noinline__ void schur_mem(const double *P, double *C, size_t st, int rp,
+                                       typename Tier::T a, typename Tier::T b,
+                                       typename Tier::T d, typename Tier::T y) {
+  if (!schur_try<Tier, Tier::RREG + 1>(rp, P, C, st, a, b, d, y)) schur_mem_loop<Tier>(P, C, st, rp, a, b, d, y);
 }
 
 // per-thread stack extent (in entries) of a walk over r modes
@@ -288,7 +387,7 @@ __device__ void dfs_walk(double *S, size_t st, int r, typename Tier::T t, int pa
       const T b = Tier::ld(P, ix(2 * cur + 1, 2 * cur), st);
       const T d = Tier::ld(P, ix(2 * cur, 2 * cur), st);
       const T det2 = Tier::det2(a, b, d);
-      if (Tier::bad(det2)) Sm.flags |= ST_NOTPD;
+      if (Tier::bad(det2) || Tier::bad(a)) Sm.flags |= ST_NOTPD;
       const T y = Tier::rsqrt(det2);
       const T tc = Tier::mul(t, y);
       Tier::acc(Sm, tc, ((k ^ (par + 1)) & 1) != 0);

@@ -26,5 +26,6 @@ void launch_finalize(const unsigned long long *block_part, int nblocks, int k, i
                      const int *status, tor_result *out, unsigned long long *total8, cudaStream_t s);
 void launch_dfma_peak(double *sink, int grid, int block, int iters, cudaStream_t s);
 int scratch_entries(int tier, int k, int r1);
+int dfs_max_blocks_per_sm(int tier, int block);
 
 }  // namespace tor

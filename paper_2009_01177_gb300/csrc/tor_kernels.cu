@@ -95,7 +95,7 @@ k_dfs(const double *__restrict__ B, const double *__restrict__ Blo, int k, int r
       const T b = Tier::ld(S, ix(2 * rp + 1, 2 * rp), st);
       const T d = Tier::ld(S, ix(2 * rp, 2 * rp), st);
       const T det2 = Tier::det2(a, b, d);
-      if (Tier::bad(det2)) Sm.flags |= ST_NOTPD;
+      if (Tier::bad(det2) || Tier::bad(a)) Sm.flags |= ST_NOTPD;
       const T y = Tier::rsqrt(det2);
       t = Tier::mul(t, y);
       if (rp > 0) schur_mem<Tier>(S, S, st, rp, a, b, d, y);
@@ -193,6 +193,14 @@ void launch_dfs(int tier, int grid, int block, const double *B, const double *Bl
     k_dfs<TierDD><<<grid, block, 0, s>>>(B, Blo, k, r1, c0, c1, scratch, block_part, chunk_part, status);
   else
     k_dfs<TierF64><<<grid, block, 0, s>>>(B, Blo, k, r1, c0, c1, scratch, block_part, chunk_part, status);
+}
+
+int dfs_max_blocks_per_sm(int tier, int block) {
+  int n = 0;
+  cudaError_t e = (tier == TOR_PREC_DD)
+                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dfs<TierDD>, block, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dfs<TierF64>, block, 0);
+  return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
 void launch_finalize(const unsigned long long *block_part, int nblocks, int k, int tier,
