@@ -147,6 +147,25 @@ int tor_chunks(tor_ctx *ctx, const double *O, int k, int ld, int layout, int pre
                int chunk_bits, uint64_t c_begin, uint64_t c_end, cudaStream_t stream,
                uint64_t *part_dev);
 
+/*
+ * tor_single_noalloc: tor_single_async for callers that cannot allocate
+ * device memory (no context; the paper has no counterpart -- this is a
+ * library-integration entry point).  It performs no cudaMalloc or cudaFree:
+ * all scratch lives in one fixed 48 MiB device array inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ *   O        dev  2k x 2k FP64, leading dimension ld, in `layout` order.
+ *   prec     TOR_PREC_FP64 or TOR_PREC_DD.
+ *   out_dev  dev  one tor_result, valid after `stream` is synchronised.
+ * Runs on the current device.  Instances whose scratch exceeds the array are
+ * rejected with TOR_EINVAL (on a 152-SM GB300: FP64 up to k = 25,
+ * double-double up to k = 17).  All calls share the array: calls that
+ * overlap on the GPU race and must be serialised by the caller.  The first
+ * call on a device looks up the array's address; make it before any stream
+ * capture.  Results equal tor_single's for the same tier.
+ */
+int tor_single_noalloc(const double *O, int k, int ld, int layout, int prec,
+                       cudaStream_t stream, tor_result *out_dev);
+
 /* Convert one 256-bit fixed-point pair (8 limbs as written by tor_chunks,
  * possibly summed over shards) to a tor_result (host, no GPU needed). */
 int tor_fixed_to_result(const uint64_t *limbs8, int k, int tier, tor_result *out);

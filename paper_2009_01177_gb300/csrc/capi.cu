@@ -34,6 +34,11 @@ struct Buf {
 
 }  // namespace
 
+int tor::record_error(int code, const char *msg) {
+  snprintf(g_err, sizeof(g_err), "%s", msg);
+  return code;
+}
+
 struct tor_ctx {
   int device = 0;
   int sms = 0;

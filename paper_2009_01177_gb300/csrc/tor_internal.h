@@ -27,5 +27,7 @@ void launch_finalize(const unsigned long long *block_part, int nblocks, int k, i
 void launch_dfma_peak(double *sink, int grid, int block, int iters, cudaStream_t s);
 int scratch_entries(int tier, int k, int r1);
 int dfs_max_blocks_per_sm(int tier, int block);
+// store a message for tor_last_error() on the calling thread; returns code
+int record_error(int code, const char *msg);
 
 }  // namespace tor

@@ -89,6 +89,7 @@ SIGNATURES = {
     "tor_batch": (_I, [_VP, _VP, _VP, _VP, _I, _I, _I, _D, _VP, _VP]),
     "tor_bounds": (_I, [_VP, _VP, _VP, _VP, _I, _I, _D, _VP, _VP]),
     "tor_fp64_peak": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "tor_single_noalloc": (_I, [_VP, _I, _I, _I, _I, _VP, _VP]),
     "tor_set_timing": (_I, [_VP, _I]),
     "tor_walk_time": (_I, [_VP, ctypes.POINTER(ctypes.c_float)]),
 }
@@ -199,6 +200,20 @@ class Context:
         r, c = ctypes.c_double(), ctypes.c_double()
         _check(self.lib.tor_fp64_peak(self.h, ctypes.byref(r), ctypes.byref(c)))
         return r.value, c.value
+
+
+def single_noalloc(O: torch.Tensor, out: torch.Tensor, prec: str = "fp64", layout: str = "xxpp",
+                   stream=None):
+    """tor_single_noalloc: enqueue Tor(O) with no device allocation; result bytes into `out`.
+
+    For callers that cannot allocate device memory: all scratch comes from a
+    fixed array inside the library.  Calls on one device must not overlap.
+    """
+    k, ld = _mat(O)
+    if out.dtype != torch.uint8 or out.numel() < RESULT_BYTES or not out.is_cuda:
+        raise ValueError(f"out must be a uint8 CUDA tensor of >= {RESULT_BYTES} bytes")
+    _check(load_library().tor_single_noalloc(O.data_ptr(), k, ld, _LAYOUT[layout], _PREC[prec],
+                                             _stream(stream), out.data_ptr()))
 
 
 def fixed_to_result(limbs8, k: int, tier: str = "fp64") -> TorResult:
