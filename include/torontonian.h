@@ -110,8 +110,12 @@ int tor_set_chunk_bits(tor_ctx *ctx, int chunk_bits);
 /*
  * tor_single: Tor of one 2k x 2k matrix (Eq. 2).
  *   O     dev  2k x 2k FP64, leading dimension ld, in `layout` order.
- *   prec  TOR_PREC_FP64, TOR_PREC_DD, or TOR_PREC_AUTO (the FP32 bound pass
- *         of tor_bounds picks the tier for tolerance `tol`).
+ *   prec  TOR_PREC_FP64, TOR_PREC_DD, or TOR_PREC_AUTO: the FP32 bound pass
+ *         of tor_bounds picks the starting tier for relative tolerance
+ *         `tol`; if the result's a-posteriori bound err_est exceeds
+ *         tol * |Tor| in FP64 it is recomputed in double-double, and if it
+ *         still does the call returns TOR_EPREC with the result filled in.
+ *         `tol` is ignored for the explicit tiers.
  *   out   host result; the call synchronises `stream`.
  * The 2^k subsets are split into equal prefix chunks (the high modes of the
  * subset mask fixed per chunk, Algorithm 1's balanced partition) walked
@@ -171,18 +175,45 @@ int tor_single_noalloc(const double *O, int k, int ld, int layout, int prec,
 int tor_fixed_to_result(const uint64_t *limbs8, int k, int tier, tor_result *out);
 
 /*
- * tor_batch: Tor of n matrices of different k in one launch sequence.
- *   O     dev  array of n device pointers (each 2k_i x 2k_i FP64).
+ * tor_batch: Tor of n matrices of different k (e.g. the patterns a sampler
+ * proposes), scheduled on the device: a plan kernel lays all (instance,
+ * chunk) pairs on one item axis per tier, sorted by chunk size, and one
+ * persistent walk kernel per tier drains it; partial sums are added exactly
+ * per instance.  Asynchronous; no host round trip once the workspace is
+ * reserved, so the whole call can be captured in a CUDA graph.
+ *   O     dev  array of n device pointers (each 2k_i x 2k_i FP64, `layout`).
  *   k,ld  dev  arrays of n ints.
- *   out   dev  n results.
+ *   prec  TOR_PREC_FP64, TOR_PREC_DD, or TOR_PREC_AUTO (per-instance tier from
+ *         the bound pass; FP64 results whose err_est exceeds tol * |Tor| are
+ *         recomputed in double-double; results still above get status
+ *         TOR_EPREC).
+ *   out   dev  n results; per-instance status TOR_OK, TOR_ENOTPD, TOR_EPREC,
+ *         or TOR_EINVAL (k outside [0, k_max] of the reservation).
+ * Without a prior tor_batch_reserve covering n (or when n grows), the call
+ * reads k to the host once to size the workspace and synchronises `stream`.
  */
 int tor_batch(tor_ctx *ctx, const double *const *O, const int *k, const int *ld, int n,
               int layout, int prec, double tol, cudaStream_t stream, tor_result *out);
+
+/* Size the batch workspace for up to n_max instances of at most k_max clicks
+ * (allocates; call before capturing tor_batch in a CUDA graph). */
+int tor_batch_reserve(tor_ctx *ctx, int n_max, int k_max);
 
 /*
  * tor_bounds: FP32 bound pass (paper Sec. 5.1, Eq. upbound/lowbound; Sec. 5.4
  * Eq. bitlen) for n matrices; picks the tier needed for tolerance `tol`.
  *   O, k, ld  dev arrays as for tor_batch.   out  dev, n bounds.
+ * Per instance: tau_j = 1/sqrt(det B_jj) of each mode's 2x2 block of
+ * B = I - O; log_tor_est = sum ln(tau_j - 1); log_kappa_est =
+ * sum ln(tau_j + 1) - log_tor_est; log_tmax = -1/2 ln det B from an FP32
+ * Cholesky; bits_needed = log2 kappa_est + log2(4k) + log2(1/tol); tier =
+ * TOR_PREC_FP64 if bits_needed <= 72 (FP64's 52 bits plus 20 bits of slack
+ * for the estimate's pessimism; AUTO callers verify the result's
+ * a-posteriori bound and escalate), else TOR_PREC_DD.  B not positive definite in
+ * FP32 gives bits_needed = +inf and tier TOR_PREC_DD.  An instance with k
+ * outside [0, TOR_MAX_K] or a null matrix gets tier 0 and NaN fields.
+ * The estimates are heuristic: on Haar-mixed lossy GBS states kappa_est
+ * over-estimates the true condition number by 10^2 to 10^13.
  */
 int tor_bounds(tor_ctx *ctx, const double *const *O, const int *k, const int *ld, int n,
                int layout, double tol, cudaStream_t stream, tor_bound *out);

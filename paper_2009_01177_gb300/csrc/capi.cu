@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <new>
 #include "tor_internal.h"
+#include "tor_walk.cuh"
 
 namespace {
 
@@ -45,9 +46,16 @@ struct tor_ctx {
   int threads_per_block = 128;
   int blocks_per_sm = 4;  // clamped to the kernel's occupancy at launch
   int chunk_bits = -1;  // -1: automatic
-  Buf B, Blo, scratch, block_part, status, result, total8;
+  Buf B, Blo, scratch, block_part, status, result, total8, bound;
   bool timing = false, timed = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // batch workspace (tor_batch_reserve)
+  int batch_nmax = 0, batch_kmax = -1;
+  Buf batch, batch_scratch;
+  tor::BatchPlan plan{};
+  tor_bound *bounds_dev = nullptr;
+  unsigned char *r1_table_dev = nullptr;
+  unsigned char r1_table[3][65];  // walked modes per chunk, by tier and k
 };
 
 namespace {
@@ -143,6 +151,11 @@ int tor_create(tor_ctx **out, int device) {
   tor_ctx *c = new (std::nothrow) tor_ctx();
   if (!c) return fail(TOR_ENOMEM, "host allocation failed");
   c->device = device;
+  for (int kk = 0; kk <= 64; ++kk) {
+    c->r1_table[0][kk] = 0;
+    c->r1_table[TOR_PREC_FP64][kk] = (unsigned char)(kk < 14 ? kk : 14);
+    c->r1_table[TOR_PREC_DD][kk] = (unsigned char)(kk < 12 ? kk : 12);
+  }
   cudaError_t e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess) {
     delete c;
@@ -156,7 +169,8 @@ void tor_destroy(tor_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
-  Buf *bufs[] = {&c->B, &c->Blo, &c->scratch, &c->block_part, &c->status, &c->result, &c->total8};
+  Buf *bufs[] = {&c->B, &c->Blo, &c->scratch, &c->block_part, &c->status, &c->result, &c->total8, &c->bound,
+                 &c->batch, &c->batch_scratch};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -226,6 +240,17 @@ int tor_single_async(tor_ctx *ctx, const double *O, int k, int ld, int layout, i
   return TOR_OK;
 }
 
+// run one tier synchronously into *out
+static int single_sync(tor_ctx *ctx, const double *O, int k, int ld, int layout, int tier, cudaStream_t s,
+                       tor_result *out) {
+  int rc;
+  if ((rc = ensure(ctx, ctx->result, sizeof(tor_result)))) return rc;
+  if ((rc = tor_single_async(ctx, O, k, ld, layout, tier, s, (tor_result *)ctx->result.p))) return rc;
+  CK(cudaMemcpyAsync(out, ctx->result.p, sizeof(tor_result), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return TOR_OK;
+}
+
 int tor_single(tor_ctx *ctx, const double *O, int k, int ld, int layout, int prec, double tol,
                cudaStream_t s, tor_result *out) {
   int rc = check_common(ctx, O, k, ld, layout);
@@ -233,15 +258,36 @@ int tor_single(tor_ctx *ctx, const double *O, int k, int ld, int layout, int pre
   if (!out) return fail(TOR_EINVAL, "null result pointer");
   if (prec != TOR_PREC_AUTO && prec != TOR_PREC_FP64 && prec != TOR_PREC_DD)
     return fail(TOR_EINVAL, "bad precision %d", prec);
-  (void)tol;
-  const int tier = pick_tier(prec);
-  if ((rc = ensure(ctx, ctx->result, sizeof(tor_result)))) return rc;
-  if ((rc = tor_single_async(ctx, O, k, ld, layout, tier, s, (tor_result *)ctx->result.p))) return rc;
-  CK(cudaMemcpyAsync(out, ctx->result.p, sizeof(tor_result), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  int tier = prec;
+  if (prec == TOR_PREC_AUTO) {
+    if (!(tol > 0.0)) return fail(TOR_EINVAL, "TOR_PREC_AUTO needs a tolerance tol > 0");
+    tier = TOR_PREC_FP64;
+    if (k > 0) {  // FP32 bound pass picks the starting tier
+      CK(cudaSetDevice(ctx->device));
+      if ((rc = ensure(ctx, ctx->bound, sizeof(tor_bound)))) return rc;
+      if (tor::launch_bounds_single(O, k, ld, layout, tol, (tor_bound *)ctx->bound.p, s))
+        return fail(TOR_ECUDA, "bound pass launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+      tor_bound bd;
+      CK(cudaMemcpyAsync(&bd, ctx->bound.p, sizeof(bd), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      tier = (bd.tier == TOR_PREC_FP64) ? TOR_PREC_FP64 : TOR_PREC_DD;
+    }
+  }
+  if ((rc = single_sync(ctx, O, k, ld, layout, tier, s, out))) return rc;
   if (out->status != TOR_OK)
     return fail(out->status, "instance status %d (%s)", out->status,
                 out->status == TOR_ENOTPD ? "some I - O_Z is not positive definite" : "term out of range");
+  if (prec == TOR_PREC_AUTO) {
+    const double mag = out->hi < 0 ? -out->hi : out->hi;
+    if (tier == TOR_PREC_FP64 && out->err_est > tol * mag) {  // a-posteriori escalation
+      tier = TOR_PREC_DD;
+      if ((rc = single_sync(ctx, O, k, ld, layout, tier, s, out))) return rc;
+    }
+    const double mag2 = out->hi < 0 ? -out->hi : out->hi;
+    if (out->err_est > tol * mag2)
+      return fail(TOR_EPREC, "error bound %.3e exceeds tol * |Tor| = %.3e even in double-double",
+                  out->err_est, tol * mag2);
+  }
   return TOR_OK;
 }
 
@@ -271,16 +317,122 @@ int tor_fixed_to_result(const uint64_t *limbs8, int k, int tier, tor_result *out
   return TOR_OK;
 }
 
+static int batch_grid(const tor_ctx *ctx, int tier) {
+  const int occ = tor::batch_walk_max_blocks_per_sm(tier, ctx->threads_per_block);
+  return ctx->sms * (ctx->blocks_per_sm < occ ? ctx->blocks_per_sm : occ);
+}
+
+int tor_batch_reserve(tor_ctx *ctx, int n_max, int k_max) {
+  if (!ctx) return fail(TOR_EINVAL, "null context");
+  if (n_max < 1) return fail(TOR_EINVAL, "n_max = %d < 1", n_max);
+  if (k_max < 0 || k_max > TOR_MAX_K) return fail(TOR_EINVAL, "k_max = %d outside [0, %d]", k_max, TOR_MAX_K);
+  CK(cudaSetDevice(ctx->device));
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t n = (size_t)n_max;
+  const size_t sz_tier = al(n), sz_r1 = al(n), sz_esc = al(n), sz_key = al(4 * n), sz_order = al(4 * n),
+               sz_flags = al(4 * n), sz_off = al(8 * (n + 1)), sz_acc = al(64 * n), sz_range = al(32),
+               sz_counter = al(16), sz_counts = al(8), sz_result = al(sizeof(tor_result) * n),
+               sz_bounds = al(sizeof(tor_bound) * n), sz_r1tab = al(3 * 65);
+  const size_t total = sz_tier + sz_r1 + sz_esc + sz_key + sz_order + sz_flags + sz_off + sz_acc + sz_range +
+                       sz_counter + sz_counts + sz_result + sz_bounds + sz_r1tab;
+  int rc;
+  if ((rc = ensure(ctx, ctx->batch, total))) return rc;
+  unsigned char *b = (unsigned char *)ctx->batch.p;
+  tor::BatchPlan &p = ctx->plan;
+  p.tier = b; b += sz_tier;
+  p.r1 = b; b += sz_r1;
+  p.escalated = b; b += sz_esc;
+  p.key = (int *)b; b += sz_key;
+  p.order = (int *)b; b += sz_order;
+  p.flags = (int *)b; b += sz_flags;
+  p.item_off = (unsigned long long *)b; b += sz_off;
+  p.acc = (unsigned long long *)b; b += sz_acc;
+  p.range = (unsigned long long *)b; b += sz_range;
+  p.counter = (unsigned long long *)b; b += sz_counter;
+  p.counts = (unsigned int *)b; b += sz_counts;
+  p.result = (tor_result *)b; b += sz_result;
+  ctx->bounds_dev = (tor_bound *)b; b += sz_bounds;
+  ctx->r1_table_dev = b;
+  CK(cudaMemcpy(ctx->r1_table_dev, ctx->r1_table, sizeof(ctx->r1_table), cudaMemcpyHostToDevice));
+  // per-thread walk stacks for the largest instance, for either tier
+  size_t scratch = 0;
+  for (int tier = TOR_PREC_FP64; tier <= TOR_PREC_DD; ++tier) {
+    int r1max = 0;
+    for (int kk = 0; kk <= k_max; ++kk) r1max = ctx->r1_table[tier][kk] > r1max ? ctx->r1_table[tier][kk] : r1max;
+    const size_t nth = (size_t)batch_grid(ctx, tier) * ctx->threads_per_block;
+    const size_t bytes = sizeof(double) * nth * (size_t)tor::scratch_entries(tier, k_max, r1max);
+    scratch = bytes > scratch ? bytes : scratch;
+  }
+  if ((rc = ensure(ctx, ctx->batch_scratch, scratch))) return rc;
+  ctx->batch_nmax = n_max;
+  ctx->batch_kmax = k_max;
+  return TOR_OK;
+}
+
 int tor_batch(tor_ctx *ctx, const double *const *O, const int *k, const int *ld, int n, int layout,
               int prec, double tol, cudaStream_t s, tor_result *out) {
-  (void)ctx; (void)O; (void)k; (void)ld; (void)n; (void)layout; (void)prec; (void)tol; (void)s; (void)out;
-  return fail(TOR_EINVAL, "tor_batch: not built yet");
+  if (!ctx) return fail(TOR_EINVAL, "null context");
+  if (n < 0) return fail(TOR_EINVAL, "n = %d < 0", n);
+  if (n == 0) return TOR_OK;
+  if (!O || !k || !ld || !out) return fail(TOR_EINVAL, "null array pointer");
+  if (layout != TOR_LAYOUT_XXPP && layout != TOR_LAYOUT_XPXP) return fail(TOR_EINVAL, "bad layout %d", layout);
+  if (prec != TOR_PREC_AUTO && prec != TOR_PREC_FP64 && prec != TOR_PREC_DD)
+    return fail(TOR_EINVAL, "bad precision %d", prec);
+  if (prec == TOR_PREC_AUTO && !(tol > 0.0)) return fail(TOR_EINVAL, "TOR_PREC_AUTO needs tol > 0");
+  CK(cudaSetDevice(ctx->device));
+  int rc;
+  if (n > ctx->batch_nmax || ctx->batch_kmax < 0) {
+    // not reserved: size the workspace from the instances (one synchronous read of k)
+    int *hk = new (std::nothrow) int[n];
+    if (!hk) return fail(TOR_ENOMEM, "host allocation failed");
+    cudaError_t e = cudaMemcpyAsync(hk, k, sizeof(int) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int kmax = ctx->batch_kmax > 0 ? ctx->batch_kmax : 0;
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+      if (hk[i] > kmax && hk[i] <= TOR_MAX_K) kmax = hk[i];
+    delete[] hk;
+    if (e != cudaSuccess) return fail(TOR_ECUDA, "reading k: %s", cudaGetErrorString(e));
+    if ((rc = tor_batch_reserve(ctx, n > ctx->batch_nmax ? n : ctx->batch_nmax, kmax))) return rc;
+  }
+  const tor::BatchPlan &p = ctx->plan;
+  const int block = ctx->threads_per_block;
+  double *scratch = (double *)ctx->batch_scratch.p;
+  const tor_bound *bd = nullptr;
+  if (prec == TOR_PREC_AUTO) {
+    if (tor::launch_bounds_batch(O, k, ld, n, layout, tol, ctx->bounds_dev, s))
+      return fail(TOR_ECUDA, "bound pass: %s", cudaGetErrorString(cudaGetLastError()));
+    bd = ctx->bounds_dev;
+  }
+  if (tor::launch_batch_plan(k, bd, n, prec, ctx->batch_kmax, ctx->r1_table_dev, 0, tol, p, s))
+    return fail(TOR_ECUDA, "plan: %s", cudaGetErrorString(cudaGetLastError()));
+  for (int tier = TOR_PREC_FP64; tier <= TOR_PREC_DD; ++tier) {
+    if (prec != TOR_PREC_AUTO && prec != tier) continue;
+    if (tor::launch_batch_walk(tier, batch_grid(ctx, tier), block, O, k, ld, layout, p, scratch, s))
+      return fail(TOR_ECUDA, "walk: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  if (tor::launch_batch_finalize(k, n, 0, 0.0, p, out, s))
+    return fail(TOR_ECUDA, "finalize: %s", cudaGetErrorString(cudaGetLastError()));
+  if (prec == TOR_PREC_AUTO) {  // second round: FP64 results that miss tol are redone in double-double
+    if (tor::launch_batch_plan(k, bd, n, prec, ctx->batch_kmax, ctx->r1_table_dev, 1, tol, p, s) ||
+        tor::launch_batch_walk(TOR_PREC_DD, batch_grid(ctx, TOR_PREC_DD), block, O, k, ld, layout, p, scratch, s) ||
+        tor::launch_batch_finalize(k, n, 0, tol, p, out, s))
+      return fail(TOR_ECUDA, "AUTO second round: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  return TOR_OK;
 }
 
 int tor_bounds(tor_ctx *ctx, const double *const *O, const int *k, const int *ld, int n, int layout,
                double tol, cudaStream_t s, tor_bound *out) {
-  (void)ctx; (void)O; (void)k; (void)ld; (void)n; (void)layout; (void)tol; (void)s; (void)out;
-  return fail(TOR_EINVAL, "tor_bounds: not built yet");
+  if (!ctx) return fail(TOR_EINVAL, "null context");
+  if (n < 0) return fail(TOR_EINVAL, "n = %d < 0", n);
+  if (n == 0) return TOR_OK;
+  if (!O || !k || !ld || !out) return fail(TOR_EINVAL, "null array pointer");
+  if (layout != TOR_LAYOUT_XXPP && layout != TOR_LAYOUT_XPXP) return fail(TOR_EINVAL, "bad layout %d", layout);
+  if (!(tol > 0.0)) return fail(TOR_EINVAL, "tol must be > 0");
+  CK(cudaSetDevice(ctx->device));
+  if (tor::launch_bounds_batch(O, k, ld, n, layout, tol, out, s))
+    return fail(TOR_ECUDA, "bound pass launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+  return TOR_OK;
 }
 
 int tor_fp64_peak(tor_ctx *ctx, double *dfma_per_s, double *sm_clock_hz) {

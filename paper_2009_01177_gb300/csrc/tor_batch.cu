@@ -1,0 +1,241 @@
+// tor_batch.cu -- many Torontonians of uneven size in one persistent launch per tier.
+//
+// Sampling produces thousands of click patterns whose click counts k vary
+// (a 2^k spread in cost).  The batch is scheduled entirely on the device so
+// that the whole sequence (bound pass, plan, walks, finalize) can be captured
+// once in a CUDA graph and replayed with new inputs, with no host round trip:
+//
+//  k_batch_plan      one block: per instance the tier (given, or from the bound
+//                    pass) and the walk depth r1 (chunks fix the top k - r1
+//                    modes, Algorithm 1's balanced partition), a counting sort
+//                    of instances by (tier, r1 descending), and an exclusive
+//                    scan of the chunk counts that lays every (instance, chunk)
+//                    pair out on one item axis per tier.  Large chunks come
+//                    first so the tail of the launch is made of small items.
+//  k_batch_walk<T>   persistent: each warp takes 32 consecutive items from an
+//                    atomic counter, finds each item's instance by binary search
+//                    over the scan, gathers I - O straight from the caller's
+//                    matrix, walks the chunk (tor_dfs.cuh), and adds the exact
+//                    256-bit partial sums into the instance's accumulator with
+//                    64-bit atomics that propagate carries.  Integer addition
+//                    is associative, so the result does not depend on which
+//                    warp ran which item.
+//  k_batch_finalize  one thread per instance: accumulator -> tor_result.
+//
+// In TOR_PREC_AUTO mode a second plan/walk/finalize round re-runs in
+// double-double every instance whose FP64 result misses the tolerance.
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "tor_dfs.cuh"
+#include "tor_internal.h"
+#include "tor_walk.cuh"
+
+namespace tor {
+
+constexpr int PLAN_THREADS = 1024;
+constexpr int NKEY = 2 * 65;  // (tier 1|2) x (64 - r1)
+
+// acc (4 limbs) += X, exactly modulo 2^256, from any number of threads
+__device__ __forceinline__ void fx_atomic_add(unsigned long long *acc, const Fx256 &X) {
+  unsigned long long carry = 0ull;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const unsigned long long v = X.w[j] + carry;
+    const unsigned long long c1 = (v < carry) ? 1ull : 0ull;  // X.w[j] == 2^64-1 with a carry in
+    unsigned long long c2 = 0ull;
+    if (v) {
+      const unsigned long long old = atomicAdd(acc + j, v);
+      c2 = (old + v < old) ? 1ull : 0ull;
+    }
+    carry = c1 + c2;
+  }
+}
+
+// mode 0: first round; mode 1: escalate failed FP64 instances to double-double
+__global__ void __launch_bounds__(PLAN_THREADS)
+k_batch_plan(const int *__restrict__ k, const tor_bound *__restrict__ bounds, int n, int prec, int kmax,
+             const unsigned char *__restrict__ r1_table /* [3][65] */, int mode, double tol,
+             BatchPlan p) {
+  __shared__ unsigned int hist[NKEY], cursor[NKEY];
+  __shared__ unsigned long long part[PLAN_THREADS];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NKEY; e += blockDim.x) hist[e] = 0;
+  __syncthreads();
+  // phase 1: per instance tier, r1, key
+  for (int i = tid; i < n; i += blockDim.x) {
+    const int ki = k[i];
+    int tier;
+    if (mode == 0) {
+      tier = (prec == TOR_PREC_AUTO) ? (bounds ? bounds[i].tier : TOR_PREC_FP64) : prec;
+      if (ki < 0 || ki > kmax) tier = 0;
+      p.tier[i] = (unsigned char)tier;
+      p.flags[i] = (tier == 0) ? ST_RANGE : 0;
+      p.escalated[i] = 0;
+    } else {
+      tier = 0;
+      const tor_result r = p.result[i];
+      const double mag = r.hi < 0 ? -r.hi : r.hi;
+      if (p.tier[i] == TOR_PREC_FP64 && r.status == TOR_OK && r.err_est > tol * mag) {
+        tier = TOR_PREC_DD;
+        p.tier[i] = TOR_PREC_DD;
+        p.escalated[i] = 1;
+        p.flags[i] = 0;
+      }
+    }
+    int key = -1, r1 = 0;
+    if (tier != 0) {
+      r1 = r1_table[tier * 65 + ki];
+      if (r1 > ki) r1 = ki;
+      key = (tier - 1) * 65 + (64 - r1);
+    }
+    p.r1[i] = (unsigned char)r1;
+    p.key[i] = key;
+    if (mode == 0 || tier != 0) {
+      unsigned long long *a = p.acc + (size_t)i * 8;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) a[j] = 0ull;
+      if (ki == 0 && tier != 0) { a[2] = 1ull; a[6] = 1ull; }  // Tor = sum t = 1 (empty set only)
+    }
+    if (key >= 0) atomicAdd(&hist[key], 1u);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned int run = 0;
+    for (int e = 0; e < NKEY; ++e) { cursor[e] = run; run += hist[e]; }
+    p.counts[0] = 0;
+    for (int e = 0; e < 65; ++e) p.counts[0] += hist[e];  // FP64 instances
+    p.counts[1] = run;                                    // all scheduled instances
+  }
+  __syncthreads();
+  // phase 2: scatter into sorted order
+  for (int i = tid; i < n; i += blockDim.x) {
+    const int key = p.key[i];
+    if (key >= 0) p.order[atomicAdd(&cursor[key], 1u)] = i;
+  }
+  __syncthreads();
+  // phase 3: exclusive scan of chunk counts over the sorted order
+  const int m = (int)p.counts[1];
+  const int per = (m + PLAN_THREADS - 1) / PLAN_THREADS;
+  const int lo = tid * per, hi = min(m, lo + per);
+  unsigned long long sum = 0;
+  for (int j = lo; j < hi; ++j) {
+    const int i = p.order[j];
+    const int ki = k[i];
+    sum += (ki == 0) ? 0ull : (1ull << (ki - p.r1[i]));
+  }
+  part[tid] = sum;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long run = 0;
+    for (int t = 0; t < PLAN_THREADS; ++t) { const unsigned long long v = part[t]; part[t] = run; run += v; }
+  }
+  __syncthreads();
+  unsigned long long run = part[tid];
+  for (int j = lo; j < hi; ++j) {
+    p.item_off[j] = run;
+    const int i = p.order[j];
+    const int ki = k[i];
+    run += (ki == 0) ? 0ull : (1ull << (ki - p.r1[i]));
+  }
+  if (tid == PLAN_THREADS - 1) p.item_off[m] = run;
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned long long split = p.item_off[p.counts[0]];
+    p.range[0] = 0ull;       // FP64 items [0, split)
+    p.range[1] = split;
+    p.range[2] = split;      // double-double items [split, total)
+    p.range[3] = p.item_off[m];
+    p.counter[0] = p.range[0];
+    p.counter[1] = p.range[2];
+  }
+}
+
+template <class Tier>
+__global__ void __launch_bounds__(128)
+k_batch_walk(const double *const *__restrict__ O, const int *__restrict__ k, const int *__restrict__ ld,
+             int layout, BatchPlan p, double *__restrict__ scratch) {
+  constexpr int t = (Tier::W == 1) ? 0 : 1;
+  const size_t st = (size_t)gridDim.x * blockDim.x;
+  const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double *S = scratch + gtid;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long end = p.range[2 * t + 1];
+  const int jlo = (t == 0) ? 0 : (int)p.counts[0];
+  const int jhi = (t == 0) ? (int)p.counts[0] : (int)p.counts[1];
+  while (true) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(p.counter + t, 32ull);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (base >= end) break;
+    const unsigned long long item = base + lane;
+    if (item < end) {
+      // last sorted position j in [jlo, jhi) with item_off[j] <= item
+      int a = jlo, b = jhi - 1;
+      while (a < b) {
+        const int mid = (a + b + 1) >> 1;
+        if (p.item_off[mid] <= item) a = mid; else b = mid - 1;
+      }
+      const int i = p.order[a];
+      const unsigned long long c = item - p.item_off[a];
+      const int ki = k[i], r1 = p.r1[i];
+      const SrcDirect src{O[i], ki, ld[i], layout};
+      Sums Sm;
+      fx_zero(Sm.tor);
+      fx_zero(Sm.sabs);
+      Sm.flags = 0;
+      walk_chunk<Tier>(src, ki, r1, c, S, st, Sm);
+      fx_atomic_add(p.acc + (size_t)i * 8, Sm.tor);
+      fx_atomic_add(p.acc + (size_t)i * 8 + 4, Sm.sabs);
+      if (Sm.flags) atomicOr(p.flags + i, Sm.flags);
+    }
+  }
+}
+
+// tol > 0: mark results whose error bound exceeds tol * |Tor| with TOR_EPREC
+__global__ void k_batch_finalize(const int *__restrict__ k, int n, int only_escalated, double tol, BatchPlan p,
+                                 tor_result *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (only_escalated && !p.escalated[i]) return;
+  tor_result r;
+  if (p.tier[i] == 0) {
+    r = tor_result{0.0, 0.0, 0.0, 0.0, 0, TOR_EINVAL};
+  } else {
+    fixed_to_result(p.acc + (size_t)i * 8, k[i], p.tier[i], p.flags[i], &r);
+    const double mag = r.hi < 0 ? -r.hi : r.hi;
+    if (tol > 0.0 && r.status == TOR_OK && r.err_est > tol * mag) r.status = TOR_EPREC;
+  }
+  out[i] = r;
+  p.result[i] = r;
+}
+
+int launch_batch_plan(const int *k, const tor_bound *bounds, int n, int prec, int kmax,
+                      const unsigned char *r1_table, int mode, double tol, const BatchPlan &p, cudaStream_t s) {
+  k_batch_plan<<<1, PLAN_THREADS, 0, s>>>(k, bounds, n, prec, kmax, r1_table, mode, tol, p);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_batch_walk(int tier, int grid, int block, const double *const *O, const int *k, const int *ld,
+                      int layout, const BatchPlan &p, double *scratch, cudaStream_t s) {
+  if (tier == TOR_PREC_DD)
+    k_batch_walk<TierDD><<<grid, block, 0, s>>>(O, k, ld, layout, p, scratch);
+  else
+    k_batch_walk<TierF64><<<grid, block, 0, s>>>(O, k, ld, layout, p, scratch);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_batch_finalize(const int *k, int n, int only_escalated, double tol, const BatchPlan &p,
+                          tor_result *out, cudaStream_t s) {
+  k_batch_finalize<<<(n + 127) / 128, 128, 0, s>>>(k, n, only_escalated, tol, p, out);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int batch_walk_max_blocks_per_sm(int tier, int block) {
+  int nb = 0;
+  cudaError_t e = (tier == TOR_PREC_DD)
+                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_walk<TierDD>, block, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_walk<TierF64>, block, 0);
+  return (e == cudaSuccess && nb > 0) ? nb : 1;
+}
+
+}  // namespace tor

@@ -14,8 +14,29 @@ __host__ __device__ inline double unit_roundoff(int tier) {
   return tier == TOR_PREC_DD ? 0x1p-104 : 0x1p-53;
 }
 
-__host__ __device__ void fixed_to_result(const unsigned long long *w8, int k, int tier, int status,
-                                         tor_result *out);
+// device arrays of a batch plan (sized for n_max instances by tor_batch_reserve)
+struct BatchPlan {
+  unsigned char *tier;            // n: 0 = not scheduled (invalid), TOR_PREC_FP64, TOR_PREC_DD
+  unsigned char *r1;              // n: walked (low) modes per chunk
+  unsigned char *escalated;       // n: re-run in double-double by the AUTO second round
+  int *key;                       // n: sort key, -1 = not scheduled
+  int *order;                     // n: instances sorted by (tier, r1 descending)
+  int *flags;                     // n: ST_* status bits
+  unsigned long long *item_off;   // n + 1: exclusive scan of chunk counts in sorted order
+  unsigned long long *acc;        // n x 8: exact fixed-point sums (signed, abs)
+  unsigned long long *range;      // 4: [fp64 begin, fp64 end, dd begin, dd end) item ranges
+  unsigned long long *counter;    // 2: work counters per tier
+  unsigned int *counts;           // 2: number of FP64 instances, number scheduled
+  tor_result *result;             // n: last finalized results (input of the AUTO round)
+};
+
+int launch_batch_plan(const int *k, const tor_bound *bounds, int n, int prec, int kmax,
+                      const unsigned char *r1_table, int mode, double tol, const BatchPlan &p, cudaStream_t s);
+int launch_batch_walk(int tier, int grid, int block, const double *const *O, const int *k, const int *ld,
+                      int layout, const BatchPlan &p, double *scratch, cudaStream_t s);
+int launch_batch_finalize(const int *k, int n, int only_escalated, double tol, const BatchPlan &p,
+                          tor_result *out, cudaStream_t s);
+int batch_walk_max_blocks_per_sm(int tier, int block);
 
 void launch_prep(const double *O, int k, int ld, int layout, double *B, double *Blo, cudaStream_t s);
 void launch_dfs(int tier, int grid, int block, const double *B, const double *Blo, int k, int r1,
@@ -27,6 +48,10 @@ void launch_finalize(const unsigned long long *block_part, int nblocks, int k, i
 void launch_dfma_peak(double *sink, int grid, int block, int iters, cudaStream_t s);
 int scratch_entries(int tier, int k, int r1);
 int dfs_max_blocks_per_sm(int tier, int block);
+int launch_bounds_batch(const double *const *O, const int *k, const int *ld, int n, int layout, double tol,
+                        tor_bound *out, cudaStream_t s);
+int launch_bounds_single(const double *O, int k, int ld, int layout, double tol, tor_bound *out,
+                         cudaStream_t s);
 // store a message for tor_last_error() on the calling thread; returns code
 int record_error(int code, const char *msg);
 

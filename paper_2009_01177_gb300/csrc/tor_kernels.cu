@@ -12,6 +12,7 @@
 #include <cstdint>
 #include "tor_dfs.cuh"
 #include "tor_internal.h"
+#include "tor_walk.cuh"
 
 namespace tor {
 
@@ -36,73 +37,27 @@ __global__ void k_prep(const double *__restrict__ O, int k, int ld, int layout,
 }
 
 template <class Tier>
-__device__ __forceinline__ typename Tier::T gather_entry(const double *__restrict__ B,
-                                                         const double *__restrict__ Blo, int n2k,
-                                                         int row, int col);
-template <>
-__device__ __forceinline__ double gather_entry<TierF64>(const double *__restrict__ B,
-                                                        const double *__restrict__, int n2k, int row,
-                                                        int col) {
-  return B[(size_t)row * n2k + col];
-}
-template <>
-__device__ __forceinline__ dd gather_entry<TierDD>(const double *__restrict__ B,
-                                                   const double *__restrict__ Blo, int n2k, int row,
-                                                   int col) {
-  return {B[(size_t)row * n2k + col], (row == col) ? Blo[row] : 0.0};
-}
-
-template <class Tier>
 __global__ void __launch_bounds__(128)
 k_dfs(const double *__restrict__ B, const double *__restrict__ Blo, int k, int r1,
       unsigned long long c_begin, unsigned long long c_end, double *__restrict__ scratch,
       unsigned long long *__restrict__ block_part, unsigned long long *__restrict__ chunk_part,
       int *__restrict__ status) {
-  using T = typename Tier::T;
   const size_t st = (size_t)gridDim.x * blockDim.x;
   const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   double *S = scratch + gtid;
-  const int n2k = 2 * k;
+  const SrcPrepped src{B, Blo, 2 * k};
 
   Fx256 tot_tor, tot_sabs;
   fx_zero(tot_tor);
   fx_zero(tot_sabs);
   int flags = 0;
-  unsigned char pm[64];
 
   for (unsigned long long c = c_begin + gtid; c < c_end; c += st) {
     Sums Sm;
     fx_zero(Sm.tor);
     fx_zero(Sm.sabs);
     Sm.flags = 0;
-    // chunk root: fixed modes r1 + j for the set bits j of c, then the low modes
-    int np = 0;
-    for (unsigned long long m = c; m; m &= m - 1) pm[np++] = (unsigned char)(r1 + __ffsll((long long)m) - 1);
-    const int n = np + r1;
-    for (int hi = 0; hi < 2 * n; ++hi) {
-      const int ph = n - 1 - (hi >> 1), qh = 1 - (hi & 1);
-      const int mh = (ph < np) ? pm[ph] : (ph - np);
-      for (int lo = 0; lo <= hi; ++lo) {
-        const int pl = n - 1 - (lo >> 1), ql = 1 - (lo & 1);
-        const int ml = (pl < np) ? pm[pl] : (pl - np);
-        Tier::stv(S, ix(hi, lo), st, gather_entry<Tier>(B, Blo, n2k, 2 * mh + qh, 2 * ml + ql));
-      }
-    }
-    T t = Tier::one();
-    for (int s = 0; s < np; ++s) {
-      const int rp = n - 1 - s;
-      const T a = Tier::ld(S, ix(2 * rp + 1, 2 * rp + 1), st);
-      const T b = Tier::ld(S, ix(2 * rp + 1, 2 * rp), st);
-      const T d = Tier::ld(S, ix(2 * rp, 2 * rp), st);
-      const T det2 = Tier::det2(a, b, d);
-      if (Tier::bad(det2) || Tier::bad(a)) Sm.flags |= ST_NOTPD;
-      const T y = Tier::rsqrt(det2);
-      t = Tier::mul(t, y);
-      if (rp > 0) schur_mem<Tier>(S, S, st, rp, a, b, d, y);
-    }
-    Tier::acc(Sm, t, ((k ^ np) & 1) != 0);
-    dfs_walk<Tier>(S, st, r1, t, np, k, Sm);
-
+    walk_chunk<Tier>(src, k, r1, c, S, st, Sm);
     if (chunk_part) {
       unsigned long long *o = chunk_part + (size_t)(c - c_begin) * 8;
 #pragma unroll
@@ -134,20 +89,6 @@ k_dfs(const double *__restrict__ B, const double *__restrict__ Blo, int k, int r
       block_part[(size_t)blockIdx.x * 8 + 4 + i] = b.w[i];
     }
   }
-}
-
-__host__ __device__ void fixed_to_result(const unsigned long long *w8, int k, int tier, int status,
-                                         tor_result *out) {
-  Fx256 a, b;
-  for (int i = 0; i < 4; ++i) { a.w[i] = w8[i]; b.w[i] = w8[4 + i]; }
-  double hi, lo;
-  fx_to_dd(a, hi, lo);
-  out->hi = hi;
-  out->lo = lo;
-  out->sum_abs = fx_to_double(b);
-  out->err_est = err_gamma(k) * unit_roundoff(tier) * out->sum_abs;
-  out->tier = tier;
-  out->status = (status & ST_NOTPD) ? TOR_ENOTPD : ((status & ST_RANGE) ? TOR_EINVAL : TOR_OK);
 }
 
 __global__ void k_finalize(const unsigned long long *__restrict__ block_part, int nblocks, int k,

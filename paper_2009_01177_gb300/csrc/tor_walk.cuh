@@ -1,0 +1,100 @@
+// tor_walk.cuh -- per-chunk walk and result conversion shared by the single,
+// sharded and batched kernels.
+#pragma once
+#include "tor_dfs.cuh"
+#include "tor_internal.h"
+
+namespace tor {
+
+// B = I - O entries as the tier's type, from the prepped mode-interleaved matrix
+struct SrcPrepped {
+  const double *__restrict__ B;
+  const double *__restrict__ Blo;
+  int n2k;
+  template <class Tier>
+  __device__ __forceinline__ typename Tier::T get(int row, int col) const;
+};
+template <>
+__device__ __forceinline__ double SrcPrepped::get<TierF64>(int row, int col) const {
+  return B[(size_t)row * n2k + col];
+}
+template <>
+__device__ __forceinline__ dd SrcPrepped::get<TierDD>(int row, int col) const {
+  return {B[(size_t)row * n2k + col], (row == col) ? Blo[row] : 0.0};
+}
+
+// B = I - O entries straight from the caller's O (xxpp or xpxp, leading dim ld):
+// 1 - o on the diagonal is rounded once (FP64) or kept exact as a two-sum (dd)
+struct SrcDirect {
+  const double *__restrict__ O;
+  int k, ld, layout;
+  __device__ __forceinline__ double o(int row, int col) const {
+    const int ri = layout == 0 ? ((row & 1) * k + (row >> 1)) : row;
+    const int rj = layout == 0 ? ((col & 1) * k + (col >> 1)) : col;
+    return O[(size_t)ri * ld + rj];
+  }
+  template <class Tier>
+  __device__ __forceinline__ typename Tier::T get(int row, int col) const;
+};
+template <>
+__device__ __forceinline__ double SrcDirect::get<TierF64>(int row, int col) const {
+  const double v = o(row, col);
+  return row == col ? 1.0 - v : -v;
+}
+template <>
+__device__ __forceinline__ dd SrcDirect::get<TierDD>(int row, int col) const {
+  const double v = o(row, col);
+  return row == col ? two_sum(1.0, -v) : dd{-v, 0.0};
+}
+
+// One chunk: the subsets whose high modes r1..k-1 are fixed by the bits of c.
+// Root: gather B over the fixed modes then the low modes into the thread's
+// stack S and eliminate the fixed modes in place; then the depth-first walk.
+template <class Tier, class Src>
+__device__ __forceinline__ void walk_chunk(const Src &src, int k, int r1, unsigned long long c, double *S,
+                                           size_t st, Sums &Sm) {
+  using T = typename Tier::T;
+  unsigned char pm[64];
+  int np = 0;
+  for (unsigned long long m = c; m; m &= m - 1) pm[np++] = (unsigned char)(r1 + __ffsll((long long)m) - 1);
+  const int n = np + r1;
+  for (int hi = 0; hi < 2 * n; ++hi) {
+    const int ph = n - 1 - (hi >> 1), qh = 1 - (hi & 1);
+    const int mh = (ph < np) ? pm[ph] : (ph - np);
+    for (int lo = 0; lo <= hi; ++lo) {
+      const int pl = n - 1 - (lo >> 1), ql = 1 - (lo & 1);
+      const int ml = (pl < np) ? pm[pl] : (pl - np);
+      Tier::stv(S, ix(hi, lo), st, src.template get<Tier>(2 * mh + qh, 2 * ml + ql));
+    }
+  }
+  T t = Tier::one();
+  for (int s = 0; s < np; ++s) {
+    const int rp = n - 1 - s;
+    const T a = Tier::ld(S, ix(2 * rp + 1, 2 * rp + 1), st);
+    const T b = Tier::ld(S, ix(2 * rp + 1, 2 * rp), st);
+    const T d = Tier::ld(S, ix(2 * rp, 2 * rp), st);
+    const T det2 = Tier::det2(a, b, d);
+    if (Tier::bad(det2) || Tier::bad(a)) Sm.flags |= ST_NOTPD;
+    const T y = Tier::rsqrt(det2);
+    t = Tier::mul(t, y);
+    if (rp > 0) schur_mem<Tier>(S, S, st, rp, a, b, d, y);
+  }
+  Tier::acc(Sm, t, ((k ^ np) & 1) != 0);
+  dfs_walk<Tier>(S, st, r1, t, np, k, Sm);
+}
+
+__host__ __device__ inline void fixed_to_result(const unsigned long long *w8, int k, int tier, int status,
+                                         tor_result *out) {
+  Fx256 a, b;
+  for (int i = 0; i < 4; ++i) { a.w[i] = w8[i]; b.w[i] = w8[4 + i]; }
+  double hi, lo;
+  fx_to_dd(a, hi, lo);
+  out->hi = hi;
+  out->lo = lo;
+  out->sum_abs = fx_to_double(b);
+  out->err_est = err_gamma(k) * unit_roundoff(tier) * out->sum_abs;
+  out->tier = tier;
+  out->status = (status & ST_NOTPD) ? TOR_ENOTPD : ((status & ST_RANGE) ? TOR_EINVAL : TOR_OK);
+}
+
+}  // namespace tor

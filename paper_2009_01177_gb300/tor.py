@@ -88,6 +88,7 @@ SIGNATURES = {
     "tor_fixed_to_result": (_I, [ctypes.POINTER(_U64), _I, _I, ctypes.POINTER(TorResultC)]),
     "tor_batch": (_I, [_VP, _VP, _VP, _VP, _I, _I, _I, _D, _VP, _VP]),
     "tor_bounds": (_I, [_VP, _VP, _VP, _VP, _I, _I, _D, _VP, _VP]),
+    "tor_batch_reserve": (_I, [_VP, _I, _I]),
     "tor_fp64_peak": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "tor_single_noalloc": (_I, [_VP, _I, _I, _I, _I, _VP, _VP]),
     "tor_set_timing": (_I, [_VP, _I]),
@@ -128,9 +129,16 @@ def _mat(O: torch.Tensor):
         raise ValueError("O must be a 2-D float64 CUDA tensor")
     if O.shape[0] != O.shape[1] or O.shape[0] % 2:
         raise ValueError("O must be 2k x 2k")
+    if O.shape[0] == 0:
+        return 0, 1
     if O.stride(1) != 1:
         raise ValueError("O must be row-major (unit column stride)")
     return O.shape[0] // 2, O.stride(0)
+
+
+def results_from_tensor(out: torch.Tensor, n: int):
+    raw = out.cpu().numpy().tobytes()
+    return [TorResult.from_bytes(raw[i * RESULT_BYTES:(i + 1) * RESULT_BYTES]) for i in range(n)]
 
 
 class Context:
@@ -186,6 +194,52 @@ class Context:
         _check(self.lib.tor_chunks(self.h, O.data_ptr(), k, ld, _LAYOUT[layout], _PREC[prec],
                                    chunk_bits, c_begin, c_end, _stream(stream), part.data_ptr()))
         return part
+
+    def bounds(self, Os, tol: float = 1e-10, layout: str = "xxpp", stream=None):
+        """FP32 bound pass for a list of 2k x 2k float64 CUDA tensors; returns a list of dicts."""
+        n = len(Os)
+        if n == 0:
+            return []
+        dev = Os[0].device
+        ptrs = torch.tensor([O.data_ptr() for O in Os], dtype=torch.int64, device=dev)
+        ks = torch.tensor([_mat(O)[0] for O in Os], dtype=torch.int32, device=dev)
+        lds = torch.tensor([_mat(O)[1] for O in Os], dtype=torch.int32, device=dev)
+        out = torch.zeros(n * BOUND_BYTES, dtype=torch.uint8, device=dev)
+        _check(self.lib.tor_bounds(self.h, ptrs.data_ptr(), ks.data_ptr(), lds.data_ptr(), n,
+                                   _LAYOUT[layout], tol, _stream(stream), out.data_ptr()))
+        raw = out.cpu().numpy().tobytes()
+        res = []
+        for i in range(n):
+            b = TorBoundC.from_buffer_copy(raw[i * BOUND_BYTES:(i + 1) * BOUND_BYTES])
+            res.append({f: getattr(b, f) for f, _ in TorBoundC._fields_})
+        return res
+
+    def batch_reserve(self, n_max: int, k_max: int):
+        """Size the batch workspace once (then tor_batch allocates nothing and is capturable)."""
+        _check(self.lib.tor_batch_reserve(self.h, n_max, k_max))
+
+    def batch_async(self, ptrs: torch.Tensor, ks: torch.Tensor, lds: torch.Tensor, out: torch.Tensor,
+                    prec: str = "fp64", tol: float = 1e-10, layout: str = "xxpp", stream=None):
+        """tor_batch on device arrays: ptrs int64, ks/lds int32, out uint8 (n * RESULT_BYTES)."""
+        n = ptrs.numel()
+        if out.numel() < n * RESULT_BYTES:
+            raise ValueError("out too small")
+        _check(self.lib.tor_batch(self.h, ptrs.data_ptr(), ks.data_ptr(), lds.data_ptr(), n, _LAYOUT[layout],
+                                  _PREC[prec], tol, _stream(stream), out.data_ptr()))
+
+    def batch(self, Os, prec: str = "fp64", tol: float = 1e-10, layout: str = "xxpp", stream=None):
+        """Tor of a list of 2k x 2k float64 CUDA tensors (blocking); returns a list of TorResult."""
+        n = len(Os)
+        if n == 0:
+            return []
+        dev = Os[0].device
+        ptrs = torch.tensor([O.data_ptr() for O in Os], dtype=torch.int64, device=dev)
+        ks = torch.tensor([_mat(O)[0] for O in Os], dtype=torch.int32, device=dev)
+        lds = torch.tensor([_mat(O)[1] for O in Os], dtype=torch.int32, device=dev)
+        out = torch.zeros(n * RESULT_BYTES, dtype=torch.uint8, device=dev)
+        self.batch_async(ptrs, ks, lds, out, prec=prec, tol=tol, layout=layout, stream=stream)
+        raw = out.cpu().numpy().tobytes()
+        return [TorResult.from_bytes(raw[i * RESULT_BYTES:(i + 1) * RESULT_BYTES]) for i in range(n)]
 
     def set_timing(self, on: bool):
         _check(self.lib.tor_set_timing(self.h, int(bool(on))))

@@ -1,0 +1,134 @@
+"""GPU tests of tor_batch: many Torontonians of uneven k in one scheduled launch."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2009_01177_gb300 import gbs_inputs as gi
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(cuda_lib):
+    c = cuda_lib.Context(0)
+    yield c
+    c.close()
+
+
+def mats_uneven(seed=4, n=40, k_lo=0, k_hi=16):
+    st = gi.lossy_gbs_state(100, 0.6, 1.2, 0.3, seed)
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        k = int(rng.integers(k_lo, k_hi + 1))
+        out.append(gi.select(st.O, np.sort(rng.choice(100, size=k, replace=False))))
+    return out
+
+
+def err(r, ref):
+    return abs(float(Fraction(r.hi) + Fraction(r.lo) - Fraction(ref.hi) - Fraction(ref.lo)))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "dd"])
+def test_batch_matches_single_and_oracle(ctx, prec):
+    mats = mats_uneven()
+    dmats = [torch.from_numpy(O).cuda() for O in mats]
+    res = ctx.batch(dmats, prec=prec)
+    for i, (O, Od, r) in enumerate(zip(mats, dmats, res)):
+        assert r.status == 0, (i, r)
+        s = ctx.single(Od, prec=prec) if O.shape[0] else None
+        if s is not None:
+            assert abs((r.hi - s.hi) + (r.lo - s.lo)) <= r.err_est + s.err_est
+            assert abs(r.sum_abs - s.sum_abs) <= 1e-12 * s.sum_abs
+        if O.shape[0] <= 24:
+            ref = oracle.tor(O)
+            assert err(r, ref) <= r.err_est, (i, O.shape[0] // 2)
+
+
+def test_batch_is_deterministic(ctx):
+    dmats = [torch.from_numpy(O).cuda() for O in mats_uneven(seed=9, n=64, k_hi=20)]
+    a = ctx.batch(dmats)
+    b = ctx.batch(dmats)
+    assert [(x.hi, x.lo, x.sum_abs) for x in a] == [(x.hi, x.lo, x.sum_abs) for x in b]
+
+
+def test_batch_statuses(ctx, cuda_lib):
+    good = gi.workload_m16_k10()[2]
+    bad = 2.0 * np.eye(8)
+    dm = [torch.from_numpy(O).cuda() for O in (good, bad, np.zeros((0, 0)), good)]
+    res = ctx.batch(dm)
+    assert res[0].status == 0 and res[3].status == 0
+    assert (res[0].hi, res[0].lo) == (res[3].hi, res[3].lo)
+    assert res[1].status == cuda_lib.TOR_ENOTPD
+    assert (res[2].hi, res[2].lo, res[2].status) == (1.0, 0.0, 0)
+
+
+def test_batch_rejects_k_beyond_reservation(ctx, cuda_lib):
+    ctx.batch_reserve(8, 6)
+    mats = [gi.thermal_O(4, 0.2), gi.thermal_O(9, 0.2)]
+    dm = [torch.from_numpy(O).cuda() for O in mats]
+    ptrs = torch.tensor([O.data_ptr() for O in dm], dtype=torch.int64, device="cuda")
+    ks = torch.tensor([4, 9], dtype=torch.int32, device="cuda")
+    lds = torch.tensor([8, 18], dtype=torch.int32, device="cuda")
+    out = torch.zeros(2 * cuda_lib.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    ctx.batch_async(ptrs, ks, lds, out)
+    r = cuda_lib.results_from_tensor(out, 2)
+    assert r[0].status == 0 and abs(r[0].value - (0.25) ** 4) < 1e-14
+    assert r[1].status == cuda_lib.TOR_EINVAL
+
+
+def test_batch_auto_mixes_tiers(ctx, cuda_lib):
+    bright = gi.lossy_gbs_state(24, 1.6, 2.0, 0.9, 77)
+    mats = [gi.select(bright.O, gi.random_pattern(24, 8, s)) for s in range(4)] + mats_uneven(n=8, k_lo=6, k_hi=12)
+    dm = [torch.from_numpy(O).cuda() for O in mats]
+    tol = 1e-8
+    res = ctx.batch(dm, prec="auto", tol=tol)
+    tiers = {r.tier for r in res}
+    assert tiers == {1, 2}
+    for O, r in zip(mats, res):
+        ref = oracle.tor(O)
+        if r.status == cuda_lib.TOR_EPREC:
+            continue
+        assert r.status == 0
+        assert err(r, ref) <= r.err_est <= tol * abs(ref.value) * (1 + 1e-9)
+
+
+def test_batch_in_cuda_graph_replays_with_new_inputs(ctx, cuda_lib):
+    n, kmax = 24, 14
+    ctx.batch_reserve(n, kmax)
+    A = mats_uneven(seed=21, n=n, k_lo=2, k_hi=kmax)
+    Bm = mats_uneven(seed=22, n=n, k_lo=2, k_hi=kmax)
+    # fixed device buffers: each slot holds a 2 kmax x 2 kmax matrix; ld = 2 kmax
+    slots = torch.zeros((n, 2 * kmax, 2 * kmax), dtype=torch.float64, device="cuda")
+    ptrs = torch.tensor([slots[i].data_ptr() for i in range(n)], dtype=torch.int64, device="cuda")
+    ks = torch.zeros(n, dtype=torch.int32, device="cuda")
+    lds = torch.full((n,), 2 * kmax, dtype=torch.int32, device="cuda")
+    out = torch.zeros(n * cuda_lib.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+
+    def load(mats):
+        slots.zero_()
+        for i, O in enumerate(mats):
+            m = O.shape[0]
+            slots[i, :m, :m] = torch.from_numpy(O)
+        ks.copy_(torch.tensor([O.shape[0] // 2 for O in mats], dtype=torch.int32))
+
+    load(A)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        ctx.batch_async(ptrs, ks, lds, out, stream=s)      # warm-up outside capture
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ctx.batch_async(ptrs, ks, lds, out, stream=s)
+    for mats in (A, Bm):
+        load(mats)
+        g.replay()
+        torch.cuda.synchronize()
+        res = cuda_lib.results_from_tensor(out, n)
+        direct = ctx.batch([torch.from_numpy(O).cuda() for O in mats])
+        assert [(r.hi, r.lo) for r in res] == [(r.hi, r.lo) for r in direct]
