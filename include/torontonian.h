@@ -195,6 +195,19 @@ int tor_fixed_to_result(const uint64_t *limbs8, int k, int tier, tor_result *out
 int tor_batch(tor_ctx *ctx, const double *const *O, const int *k, const int *ld, int n,
               int layout, int prec, double tol, cudaStream_t stream, tor_result *out);
 
+/*
+ * tor_batch_patterns: tor_batch for n click patterns of one state, without
+ * forming the submatrices: O_S is gathered on the fly from the full matrix by
+ * the selection rule of Eq. 1 (rows/cols j and M + j of each clicked mode j).
+ *   O         dev  2M x 2M FP64 O = I - Sigma^-1 in xxpp order, leading dim ld.
+ *   patterns  dev  n x ceil(M/64) uint64 bitsets, bit j of word j/64 = mode j
+ *             clicked (M <= 128; at most TOR_MAX_K clicks per pattern).
+ *   out       dev  n results, Tor(O_S) of each pattern.  p(S) = Tor / sqrt(det Sigma).
+ * Same scheduling, precision and workspace rules as tor_batch.
+ */
+int tor_batch_patterns(tor_ctx *ctx, const double *O, int M, int ld, const uint64_t *patterns, int n,
+                       int prec, double tol, cudaStream_t stream, tor_result *out);
+
 /* Size the batch workspace for up to n_max instances of at most k_max clicks
  * (allocates; call before capturing tor_batch in a CUDA graph). */
 int tor_batch_reserve(tor_ctx *ctx, int n_max, int k_max);
@@ -217,6 +230,69 @@ int tor_batch_reserve(tor_ctx *ctx, int n_max, int k_max);
  */
 int tor_bounds(tor_ctx *ctx, const double *const *O, const int *k, const int *ld, int n,
                int layout, double tol, cudaStream_t stream, tor_bound *out);
+
+/* ----------------------------------------------- learned proposal (MADE) */
+
+/*
+ * A masked autoregressive network over click patterns, the proposal of an
+ * independence Metropolis-Hastings sampler (the paper samples by MCMC,
+ * Sec. 7.1.1, without fixing the proposal; this network is the project's
+ * addition).  q(x) = prod_j Bernoulli(x_j; sigmoid(l_j(x_<j))), l from an MLP
+ * M -> hidden -> hidden -> hidden -> M with ReLU and MADE masks (input j has
+ * degree j+1, hidden unit h degree 1 + (h mod (M-1)), output j sees hidden
+ * units of degree <= j).  BF16 weights on tensor cores, FP32 accumulation,
+ * FP32 master weights with masked Adam (beta 0.9 / 0.999, eps 1e-8).
+ * Parameter order for get/set: W1[hidden x M], b1, W2, b2, W3, b3,
+ * W4[M x hidden], b4[M], row-major.  Calls run on the current device;
+ * functions with host pointers synchronise.
+ */
+typedef struct tor_mlp tor_mlp;
+int tor_mlp_create(tor_ctx *ctx, int M, int hidden, uint64_t seed, tor_mlp **out);
+void tor_mlp_destroy(tor_mlp *m);
+int tor_mlp_num_params(const tor_mlp *m);
+/* which: 0 weights, 1 gradients of the last grad/train call, 2 the 0/1 masks */
+int tor_mlp_get_params(const tor_mlp *m, float *host, int which);
+int tor_mlp_set_params(tor_mlp *m, const float *host);   /* masked entries forced to 0 */
+/* log q(x) for B patterns (dev bitsets, ceil(M/64) words each) -> dev doubles */
+int tor_mlp_logq(tor_mlp *m, const uint64_t *patterns, int B, double *logq, cudaStream_t stream);
+/* the M logits of each pattern, to host (B x M floats) */
+int tor_mlp_logits(tor_mlp *m, const uint64_t *patterns, int B, float *logits_host);
+/* gradients of L = -(sum_b w_b log q(x_b)) / sum_b w_b (w: dev, B floats); loss to host if non-null */
+int tor_mlp_grad(tor_mlp *m, const uint64_t *patterns, const float *w, int B, float *loss_host,
+                 cudaStream_t stream);
+/* one Adam step on L with learning rate lr */
+int tor_mlp_train_step(tor_mlp *m, const uint64_t *patterns, const float *w, int B, float lr,
+                       float *loss_host, cudaStream_t stream);
+/* B ancestral samples (dev bitsets out) and their log q (dev); draw j of sample b
+ * is Philox4x32-10 at (seed; step, b, j) */
+int tor_mlp_sample(tor_mlp *m, int B, uint64_t seed, uint64_t step, uint64_t *patterns, double *logq,
+                   cudaStream_t stream);
+
+/* ------------------------------------------------------------ MH sampling */
+
+/*
+ * gbs_sample_step: one independence Metropolis-Hastings step of C chains
+ * targeting p(S) = Tor(O_S) / sqrt(det Sigma) (Eq. 1).
+ *   O             dev  full 2M x 2M O = I - Sigma^-1, xxpp, leading dim ld (M <= 128).
+ *   logdet_sigma  ln det Sigma.
+ *   marg_p        dev  M single-mode click probabilities (plain proposal:
+ *                 independent Bernoulli per mode); ignored when proposal != NULL.
+ *   proposal      NULL for the plain proposal, or a tor_mlp over the same M.
+ *   patterns      dev  C x ceil(M/64) uint64 chain states (in/out).
+ *   logp, logq    dev  C doubles: ln p and ln q of the current states (in/out);
+ *                 logp = -inf marks an uninitialised chain (accepts any
+ *                 proposal with p > 0).  After retraining the network, refresh
+ *                 logq of the current states with tor_mlp_logq.
+ *   accepted      dev  C ints, 1 where the proposal was accepted.
+ *   seed, step    Philox4x32-10 key and counter: draw j of chain c is at
+ *                 (seed; step, c, j), j < M for the proposal, j = M to accept.
+ *   prec, tol     tier for the exact Torontonians, as for tor_batch.
+ * Asynchronous; the Torontonians use tor_batch_patterns' workspace rules.
+ */
+int gbs_sample_step(tor_ctx *ctx, const double *O, int M, int ld, double logdet_sigma,
+                    const double *marg_p, tor_mlp *proposal, int C, uint64_t *patterns,
+                    double *logp, double *logq, int *accepted, uint64_t seed, uint64_t step,
+                    int prec, double tol, cudaStream_t stream);
 
 /* -------------------------------------------------------------- utilities */
 

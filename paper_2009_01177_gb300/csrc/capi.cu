@@ -55,6 +55,8 @@ struct tor_ctx {
   tor::BatchPlan plan{};
   tor_bound *bounds_dev = nullptr;
   unsigned char *r1_table_dev = nullptr;
+  int *k_dev = nullptr;  // pattern mode: click counts
+  Buf mh;                // sampler: proposals, their log q, their Torontonians
   unsigned char r1_table[3][65];  // walked modes per chunk, by tier and k
 };
 
@@ -170,7 +172,7 @@ void tor_destroy(tor_ctx *c) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   Buf *bufs[] = {&c->B, &c->Blo, &c->scratch, &c->block_part, &c->status, &c->result, &c->total8, &c->bound,
-                 &c->batch, &c->batch_scratch};
+                 &c->batch, &c->batch_scratch, &c->mh};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -317,8 +319,8 @@ int tor_fixed_to_result(const uint64_t *limbs8, int k, int tier, tor_result *out
   return TOR_OK;
 }
 
-static int batch_grid(const tor_ctx *ctx, int tier) {
-  const int occ = tor::batch_walk_max_blocks_per_sm(tier, ctx->threads_per_block);
+static int batch_grid(const tor_ctx *ctx, int tier, bool patterns = false) {
+  const int occ = tor::batch_walk_max_blocks_per_sm(tier, ctx->threads_per_block, patterns);
   return ctx->sms * (ctx->blocks_per_sm < occ ? ctx->blocks_per_sm : occ);
 }
 
@@ -332,9 +334,9 @@ int tor_batch_reserve(tor_ctx *ctx, int n_max, int k_max) {
   const size_t sz_tier = al(n), sz_r1 = al(n), sz_esc = al(n), sz_key = al(4 * n), sz_order = al(4 * n),
                sz_flags = al(4 * n), sz_off = al(8 * (n + 1)), sz_acc = al(64 * n), sz_range = al(32),
                sz_counter = al(16), sz_counts = al(8), sz_result = al(sizeof(tor_result) * n),
-               sz_bounds = al(sizeof(tor_bound) * n), sz_r1tab = al(3 * 65);
+               sz_bounds = al(sizeof(tor_bound) * n), sz_r1tab = al(3 * 65), sz_k = al(4 * n);
   const size_t total = sz_tier + sz_r1 + sz_esc + sz_key + sz_order + sz_flags + sz_off + sz_acc + sz_range +
-                       sz_counter + sz_counts + sz_result + sz_bounds + sz_r1tab;
+                       sz_counter + sz_counts + sz_result + sz_bounds + sz_r1tab + sz_k;
   int rc;
   if ((rc = ensure(ctx, ctx->batch, total))) return rc;
   unsigned char *b = (unsigned char *)ctx->batch.p;
@@ -352,14 +354,16 @@ int tor_batch_reserve(tor_ctx *ctx, int n_max, int k_max) {
   p.counts = (unsigned int *)b; b += sz_counts;
   p.result = (tor_result *)b; b += sz_result;
   ctx->bounds_dev = (tor_bound *)b; b += sz_bounds;
-  ctx->r1_table_dev = b;
+  ctx->r1_table_dev = b; b += sz_r1tab;
+  ctx->k_dev = (int *)b;
   CK(cudaMemcpy(ctx->r1_table_dev, ctx->r1_table, sizeof(ctx->r1_table), cudaMemcpyHostToDevice));
   // per-thread walk stacks for the largest instance, for either tier
   size_t scratch = 0;
   for (int tier = TOR_PREC_FP64; tier <= TOR_PREC_DD; ++tier) {
     int r1max = 0;
     for (int kk = 0; kk <= k_max; ++kk) r1max = ctx->r1_table[tier][kk] > r1max ? ctx->r1_table[tier][kk] : r1max;
-    const size_t nth = (size_t)batch_grid(ctx, tier) * ctx->threads_per_block;
+    const int g0 = batch_grid(ctx, tier, false), g1 = batch_grid(ctx, tier, true);
+    const size_t nth = (size_t)(g0 > g1 ? g0 : g1) * ctx->threads_per_block;
     const size_t bytes = sizeof(double) * nth * (size_t)tor::scratch_entries(tier, k_max, r1max);
     scratch = bytes > scratch ? bytes : scratch;
   }
@@ -369,55 +373,135 @@ int tor_batch_reserve(tor_ctx *ctx, int n_max, int k_max) {
   return TOR_OK;
 }
 
-int tor_batch(tor_ctx *ctx, const double *const *O, const int *k, const int *ld, int n, int layout,
-              int prec, double tol, cudaStream_t s, tor_result *out) {
-  if (!ctx) return fail(TOR_EINVAL, "null context");
-  if (n < 0) return fail(TOR_EINVAL, "n = %d < 0", n);
-  if (n == 0) return TOR_OK;
-  if (!O || !k || !ld || !out) return fail(TOR_EINVAL, "null array pointer");
-  if (layout != TOR_LAYOUT_XXPP && layout != TOR_LAYOUT_XPXP) return fail(TOR_EINVAL, "bad layout %d", layout);
-  if (prec != TOR_PREC_AUTO && prec != TOR_PREC_FP64 && prec != TOR_PREC_DD)
-    return fail(TOR_EINVAL, "bad precision %d", prec);
-  if (prec == TOR_PREC_AUTO && !(tol > 0.0)) return fail(TOR_EINVAL, "TOR_PREC_AUTO needs tol > 0");
-  CK(cudaSetDevice(ctx->device));
-  int rc;
-  if (n > ctx->batch_nmax || ctx->batch_kmax < 0) {
-    // not reserved: size the workspace from the instances (one synchronous read of k)
-    int *hk = new (std::nothrow) int[n];
-    if (!hk) return fail(TOR_ENOMEM, "host allocation failed");
-    cudaError_t e = cudaMemcpyAsync(hk, k, sizeof(int) * n, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    int kmax = ctx->batch_kmax > 0 ? ctx->batch_kmax : 0;
-    for (int i = 0; i < n && e == cudaSuccess; ++i)
-      if (hk[i] > kmax && hk[i] <= TOR_MAX_K) kmax = hk[i];
-    delete[] hk;
-    if (e != cudaSuccess) return fail(TOR_ECUDA, "reading k: %s", cudaGetErrorString(e));
-    if ((rc = tor_batch_reserve(ctx, n > ctx->batch_nmax ? n : ctx->batch_nmax, kmax))) return rc;
-  }
+// enqueue bound pass (AUTO), plan, walks, finalize, and the AUTO second round
+static int batch_enqueue(tor_ctx *ctx, const tor::BatchInput &in, int n, int prec, double tol, cudaStream_t s,
+                         tor_result *out) {
   const tor::BatchPlan &p = ctx->plan;
+  const bool pat = in.words > 0;
   const int block = ctx->threads_per_block;
   double *scratch = (double *)ctx->batch_scratch.p;
   const tor_bound *bd = nullptr;
   if (prec == TOR_PREC_AUTO) {
-    if (tor::launch_bounds_batch(O, k, ld, n, layout, tol, ctx->bounds_dev, s))
-      return fail(TOR_ECUDA, "bound pass: %s", cudaGetErrorString(cudaGetLastError()));
+    const int rc = pat ? tor::launch_bounds_patterns(in.Ofull, in.M, in.ldfull, in.patterns, in.words, n, tol,
+                                                     ctx->bounds_dev, s)
+                       : tor::launch_bounds_batch(in.O, in.k, in.ld, n, in.layout, tol, ctx->bounds_dev, s);
+    if (rc) return fail(TOR_ECUDA, "bound pass: %s", cudaGetErrorString(cudaGetLastError()));
     bd = ctx->bounds_dev;
   }
-  if (tor::launch_batch_plan(k, bd, n, prec, ctx->batch_kmax, ctx->r1_table_dev, 0, tol, p, s))
+  if (tor::launch_batch_plan(in.k, bd, n, prec, ctx->batch_kmax, ctx->r1_table_dev, 0, tol, p, s))
     return fail(TOR_ECUDA, "plan: %s", cudaGetErrorString(cudaGetLastError()));
   for (int tier = TOR_PREC_FP64; tier <= TOR_PREC_DD; ++tier) {
     if (prec != TOR_PREC_AUTO && prec != tier) continue;
-    if (tor::launch_batch_walk(tier, batch_grid(ctx, tier), block, O, k, ld, layout, p, scratch, s))
+    if (tor::launch_batch_walk(tier, batch_grid(ctx, tier, pat), block, in, p, scratch, s))
       return fail(TOR_ECUDA, "walk: %s", cudaGetErrorString(cudaGetLastError()));
   }
-  if (tor::launch_batch_finalize(k, n, 0, 0.0, p, out, s))
+  if (tor::launch_batch_finalize(in.k, n, 0, 0.0, p, out, s))
     return fail(TOR_ECUDA, "finalize: %s", cudaGetErrorString(cudaGetLastError()));
   if (prec == TOR_PREC_AUTO) {  // second round: FP64 results that miss tol are redone in double-double
-    if (tor::launch_batch_plan(k, bd, n, prec, ctx->batch_kmax, ctx->r1_table_dev, 1, tol, p, s) ||
-        tor::launch_batch_walk(TOR_PREC_DD, batch_grid(ctx, TOR_PREC_DD), block, O, k, ld, layout, p, scratch, s) ||
-        tor::launch_batch_finalize(k, n, 0, tol, p, out, s))
+    if (tor::launch_batch_plan(in.k, bd, n, prec, ctx->batch_kmax, ctx->r1_table_dev, 1, tol, p, s) ||
+        tor::launch_batch_walk(TOR_PREC_DD, batch_grid(ctx, TOR_PREC_DD, pat), block, in, p, scratch, s) ||
+        tor::launch_batch_finalize(in.k, n, 0, tol, p, out, s))
       return fail(TOR_ECUDA, "AUTO second round: %s", cudaGetErrorString(cudaGetLastError()));
   }
+  return TOR_OK;
+}
+
+// not reserved (or n grew): size the workspace from the click counts, read once
+static int batch_autoreserve(tor_ctx *ctx, const int *k_dev, int n, cudaStream_t s) {
+  int *hk = new (std::nothrow) int[n];
+  if (!hk) return fail(TOR_ENOMEM, "host allocation failed");
+  cudaError_t e = cudaMemcpyAsync(hk, k_dev, sizeof(int) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int kmax = ctx->batch_kmax > 0 ? ctx->batch_kmax : 0;
+  for (int i = 0; i < n && e == cudaSuccess; ++i)
+    if (hk[i] > kmax && hk[i] <= TOR_MAX_K) kmax = hk[i];
+  delete[] hk;
+  if (e != cudaSuccess) return fail(TOR_ECUDA, "reading k: %s", cudaGetErrorString(e));
+  return tor_batch_reserve(ctx, n > ctx->batch_nmax ? n : ctx->batch_nmax, kmax);
+}
+
+static int batch_check(tor_ctx *ctx, int n, int prec, double tol) {
+  if (!ctx) return fail(TOR_EINVAL, "null context");
+  if (n < 0) return fail(TOR_EINVAL, "n = %d < 0", n);
+  if (prec != TOR_PREC_AUTO && prec != TOR_PREC_FP64 && prec != TOR_PREC_DD)
+    return fail(TOR_EINVAL, "bad precision %d", prec);
+  if (prec == TOR_PREC_AUTO && !(tol > 0.0)) return fail(TOR_EINVAL, "TOR_PREC_AUTO needs tol > 0");
+  return TOR_OK;
+}
+
+int tor_batch(tor_ctx *ctx, const double *const *O, const int *k, const int *ld, int n, int layout,
+              int prec, double tol, cudaStream_t s, tor_result *out) {
+  int rc = batch_check(ctx, n, prec, tol);
+  if (rc) return rc;
+  if (n == 0) return TOR_OK;
+  if (!O || !k || !ld || !out) return fail(TOR_EINVAL, "null array pointer");
+  if (layout != TOR_LAYOUT_XXPP && layout != TOR_LAYOUT_XPXP) return fail(TOR_EINVAL, "bad layout %d", layout);
+  CK(cudaSetDevice(ctx->device));
+  if (n > ctx->batch_nmax || ctx->batch_kmax < 0)
+    if ((rc = batch_autoreserve(ctx, k, n, s))) return rc;
+  tor::BatchInput in{O, k, ld, layout, nullptr, nullptr, 0, 0, 0};
+  return batch_enqueue(ctx, in, n, prec, tol, s, out);
+}
+
+int tor_batch_patterns(tor_ctx *ctx, const double *O, int M, int ld, const uint64_t *patterns, int n, int prec,
+                       double tol, cudaStream_t s, tor_result *out) {
+  int rc = batch_check(ctx, n, prec, tol);
+  if (rc) return rc;
+  if (n == 0) return TOR_OK;
+  if (M < 1 || M > 128) return fail(TOR_EINVAL, "M = %d outside [1, 128]", M);
+  if (!O || !patterns || !out) return fail(TOR_EINVAL, "null array pointer");
+  if (ld < 2 * M) return fail(TOR_EINVAL, "ld = %d < 2M = %d", ld, 2 * M);
+  CK(cudaSetDevice(ctx->device));
+  const int words = (M + 63) / 64;
+  if (n > ctx->batch_nmax || ctx->batch_kmax < 0) {
+    // the click counts must exist before sizing: a scratch count array first
+    Buf tmp;
+    if ((rc = ensure(ctx, tmp, sizeof(int) * (size_t)n))) return rc;
+    if (tor::launch_pattern_popcount((const unsigned long long *)patterns, n, words, (int *)tmp.p, s)) {
+      cudaFree(tmp.p);
+      return fail(TOR_ECUDA, "popcount: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    rc = batch_autoreserve(ctx, (const int *)tmp.p, n, s);
+    cudaFree(tmp.p);
+    if (rc) return rc;
+  }
+  if (tor::launch_pattern_popcount((const unsigned long long *)patterns, n, words, ctx->k_dev, s))
+    return fail(TOR_ECUDA, "popcount: %s", cudaGetErrorString(cudaGetLastError()));
+  tor::BatchInput in{nullptr, ctx->k_dev, nullptr, TOR_LAYOUT_XXPP, O, (const unsigned long long *)patterns, M, ld,
+                     words};
+  return batch_enqueue(ctx, in, n, prec, tol, s, out);
+}
+
+int gbs_sample_step(tor_ctx *ctx, const double *O, int M, int ld, double logdet_sigma, const double *marg_p,
+                    tor_mlp *proposal, int C, uint64_t *patterns, double *logp, double *logq, int *accepted,
+                    uint64_t seed, uint64_t step, int prec, double tol, cudaStream_t s) {
+  if (!ctx) return fail(TOR_EINVAL, "null context");
+  if (M < 1 || M > 128) return fail(TOR_EINVAL, "M = %d outside [1, 128]", M);
+  if (C < 0) return fail(TOR_EINVAL, "C = %d < 0", C);
+  if (C == 0) return TOR_OK;
+  if (!O || !patterns || !logp || !logq || !accepted) return fail(TOR_EINVAL, "null array pointer");
+  if (!proposal && !marg_p) return fail(TOR_EINVAL, "plain proposal needs the marginals marg_p");
+  if (proposal && tor::mlp_modes(proposal) != M) return fail(TOR_EINVAL, "proposal network has a different M");
+  CK(cudaSetDevice(ctx->device));
+  const int words = (M + 63) / 64;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t b_prop = al(sizeof(uint64_t) * words * (size_t)C), b_lq = al(sizeof(double) * (size_t)C),
+               b_res = al(sizeof(tor_result) * (size_t)C);
+  int rc;
+  if ((rc = ensure(ctx, ctx->mh, b_prop + b_lq + b_res))) return rc;
+  unsigned char *base = (unsigned char *)ctx->mh.p;
+  unsigned long long *prop = (unsigned long long *)base;
+  double *lq_prop = (double *)(base + b_prop);
+  tor_result *res = (tor_result *)(base + b_prop + b_lq);
+  if (proposal) {
+    if ((rc = tor_mlp_sample(proposal, C, seed, step, (uint64_t *)prop, lq_prop, s))) return rc;
+  } else if (tor::launch_propose_plain(marg_p, M, C, words, seed, step, prop, lq_prop, s)) {
+    return fail(TOR_ECUDA, "proposal: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  if ((rc = tor_batch_patterns(ctx, O, M, ld, (const uint64_t *)prop, C, prec, tol, s, res))) return rc;
+  if (tor::launch_accept(C, M, words, logdet_sigma, res, prop, lq_prop, (unsigned long long *)patterns, logp, logq,
+                         accepted, seed, step, s))
+    return fail(TOR_ECUDA, "accept: %s", cudaGetErrorString(cudaGetLastError()));
   return TOR_OK;
 }
 

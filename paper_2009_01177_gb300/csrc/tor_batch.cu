@@ -150,10 +150,9 @@ k_batch_plan(const int *__restrict__ k, const tor_bound *__restrict__ bounds, in
   }
 }
 
-template <class Tier>
+template <class Tier, bool PAT>
 __global__ void __launch_bounds__(128)
-k_batch_walk(const double *const *__restrict__ O, const int *__restrict__ k, const int *__restrict__ ld,
-             int layout, BatchPlan p, double *__restrict__ scratch) {
+k_batch_walk(BatchInput in, BatchPlan p, double *__restrict__ scratch) {
   constexpr int t = (Tier::W == 1) ? 0 : 1;
   const size_t st = (size_t)gridDim.x * blockDim.x;
   const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -177,13 +176,23 @@ k_batch_walk(const double *const *__restrict__ O, const int *__restrict__ k, con
       }
       const int i = p.order[a];
       const unsigned long long c = item - p.item_off[a];
-      const int ki = k[i], r1 = p.r1[i];
-      const SrcDirect src{O[i], ki, ld[i], layout};
+      const int ki = in.k[i], r1 = p.r1[i];
       Sums Sm;
       fx_zero(Sm.tor);
       fx_zero(Sm.sabs);
       Sm.flags = 0;
-      walk_chunk<Tier>(src, ki, r1, c, S, st, Sm);
+      if constexpr (PAT) {
+        unsigned char gm[64];
+        int m = 0;
+        for (int w = 0; w < in.words; ++w)
+          for (unsigned long long bits = in.patterns[(size_t)i * in.words + w]; bits && m < 64; bits &= bits - 1)
+            gm[m++] = (unsigned char)(64 * w + __ffsll((long long)bits) - 1);
+        const SrcPattern src{in.Ofull, in.M, in.ldfull, gm};
+        walk_chunk<Tier>(src, ki, r1, c, S, st, Sm);
+      } else {
+        const SrcDirect src{in.O[i], ki, in.ld[i], in.layout};
+        walk_chunk<Tier>(src, ki, r1, c, S, st, Sm);
+      }
       fx_atomic_add(p.acc + (size_t)i * 8, Sm.tor);
       fx_atomic_add(p.acc + (size_t)i * 8 + 4, Sm.sabs);
       if (Sm.flags) atomicOr(p.flags + i, Sm.flags);
@@ -215,12 +224,30 @@ int launch_batch_plan(const int *k, const tor_bound *bounds, int n, int prec, in
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_batch_walk(int tier, int grid, int block, const double *const *O, const int *k, const int *ld,
-                      int layout, const BatchPlan &p, double *scratch, cudaStream_t s) {
-  if (tier == TOR_PREC_DD)
-    k_batch_walk<TierDD><<<grid, block, 0, s>>>(O, k, ld, layout, p, scratch);
-  else
-    k_batch_walk<TierF64><<<grid, block, 0, s>>>(O, k, ld, layout, p, scratch);
+int launch_batch_walk(int tier, int grid, int block, const BatchInput &in, const BatchPlan &p, double *scratch,
+                      cudaStream_t s) {
+  const bool pat = in.words > 0;
+  if (tier == TOR_PREC_DD) {
+    if (pat) k_batch_walk<TierDD, true><<<grid, block, 0, s>>>(in, p, scratch);
+    else k_batch_walk<TierDD, false><<<grid, block, 0, s>>>(in, p, scratch);
+  } else {
+    if (pat) k_batch_walk<TierF64, true><<<grid, block, 0, s>>>(in, p, scratch);
+    else k_batch_walk<TierF64, false><<<grid, block, 0, s>>>(in, p, scratch);
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+__global__ void k_pattern_popcount(const unsigned long long *__restrict__ patterns, int n, int words,
+                                   int *__restrict__ k) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c = 0;
+  for (int w = 0; w < words; ++w) c += __popcll(patterns[(size_t)i * words + w]);
+  k[i] = c;
+}
+
+int launch_pattern_popcount(const unsigned long long *patterns, int n, int words, int *k, cudaStream_t s) {
+  k_pattern_popcount<<<(n + 255) / 256, 256, 0, s>>>(patterns, n, words, k);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -230,11 +257,15 @@ int launch_batch_finalize(const int *k, int n, int only_escalated, double tol, c
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int batch_walk_max_blocks_per_sm(int tier, int block) {
+int batch_walk_max_blocks_per_sm(int tier, int block, bool patterns) {
   int nb = 0;
-  cudaError_t e = (tier == TOR_PREC_DD)
-                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_walk<TierDD>, block, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_walk<TierF64>, block, 0);
+  cudaError_t e;
+  if (tier == TOR_PREC_DD)
+    e = patterns ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_walk<TierDD, true>, block, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_walk<TierDD, false>, block, 0);
+  else
+    e = patterns ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_walk<TierF64, true>, block, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_walk<TierF64, false>, block, 0);
   return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 

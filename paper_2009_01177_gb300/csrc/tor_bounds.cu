@@ -37,10 +37,29 @@ namespace tor {
 constexpr int BOUNDS_THREADS = 64;
 constexpr float FP64_ROUTE_BITS = 52.f + 20.f;  // optimistic FP64 attempt, see above
 
-__device__ void bounds_one(const double *__restrict__ O, int k, int ld, int layout, double tol,
-                           float *sB, tor_bound *out) {
+// O entries of one instance in mode-interleaved local coordinates (row = 2m + q)
+struct OInstance {
+  const double *O;
+  int k, ld, layout;
+  __device__ double operator()(int r, int c) const {
+    const int ri = (layout == 0) ? ((r & 1) * k + (r >> 1)) : r;
+    const int rj = (layout == 0) ? ((c & 1) * k + (c >> 1)) : c;
+    return O[(size_t)ri * ld + rj];
+  }
+};
+struct OPattern {  // O_S of a click pattern: local mode m is global mode gm[m] (rows gm[m], M + gm[m])
+  const double *O;
+  int M, ld;
+  const unsigned char *gm;
+  __device__ double operator()(int r, int c) const {
+    return O[(size_t)((r & 1) * M + gm[r >> 1]) * ld + (c & 1) * M + gm[c >> 1]];
+  }
+};
+
+template <class Get>
+__device__ void bounds_one(const Get &getO, bool valid, int k, double tol, float *sB, tor_bound *out) {
   const int tid = threadIdx.x;
-  if (k < 0 || k > TOR_MAX_K || !O) {  // invalid instance: tier 0, bits_needed NaN
+  if (k < 0 || k > TOR_MAX_K || !valid) {  // invalid instance: tier 0, bits_needed NaN
     if (tid == 0) *out = tor_bound{NAN, NAN, NAN, NAN, 0};
     return;
   }
@@ -48,9 +67,7 @@ __device__ void bounds_one(const double *__restrict__ O, int k, int ld, int layo
   // B = I - O in FP32, mode-interleaved, full square in shared memory
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int r = e / n, c = e % n;
-    const int ri = (layout == 0) ? ((r & 1) * k + (r >> 1)) : r;
-    const int rj = (layout == 0) ? ((c & 1) * k + (c >> 1)) : c;
-    sB[e] = (float)((r == c ? 1.0 : 0.0) - O[(size_t)ri * ld + rj]);
+    sB[e] = (float)((r == c ? 1.0 : 0.0) - getO(r, c));
   }
   __syncthreads();
   // per-mode factors tau_j (warp 0 reduces the logs)
@@ -107,13 +124,34 @@ k_bounds_batch(const double *const *__restrict__ O, const int *__restrict__ k, c
                int layout, double tol, tor_bound *__restrict__ out) {
   extern __shared__ float sB[];
   const int i = blockIdx.x;
-  bounds_one(O[i], k[i], ld[i], layout, tol, sB, out + i);
+  bounds_one(OInstance{O[i], k[i], ld[i], layout}, O[i] != nullptr, k[i], tol, sB, out + i);
 }
 
 __global__ void __launch_bounds__(BOUNDS_THREADS)
 k_bounds_single(const double *__restrict__ O, int k, int ld, int layout, double tol, tor_bound *__restrict__ out) {
   extern __shared__ float sB[];
-  bounds_one(O, k, ld, layout, tol, sB, out);
+  bounds_one(OInstance{O, k, ld, layout}, O != nullptr, k, tol, sB, out);
+}
+
+__global__ void __launch_bounds__(BOUNDS_THREADS)
+k_bounds_patterns(const double *__restrict__ Ofull, int M, int ld, const unsigned long long *__restrict__ patterns,
+                  int words, double tol, tor_bound *__restrict__ out) {
+  extern __shared__ float sB[];
+  __shared__ unsigned char gm[TOR_MAX_K];
+  __shared__ int s_k;
+  const int i = blockIdx.x;
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int w = 0; w < words; ++w)
+      for (unsigned long long bits = patterns[(size_t)i * words + w]; bits; bits &= bits - 1) {
+        if (m < TOR_MAX_K) gm[m] = (unsigned char)(64 * w + __ffsll((long long)bits) - 1);
+        ++m;
+      }
+    s_k = m;
+  }
+  __syncthreads();
+  const int k = s_k;
+  bounds_one(OPattern{Ofull, M, ld, gm}, k <= TOR_MAX_K, k, tol, sB, out + i);
 }
 
 int launch_bounds_batch(const double *const *O, const int *k, const int *ld, int n, int layout, double tol,
@@ -121,6 +159,14 @@ int launch_bounds_batch(const double *const *O, const int *k, const int *ld, int
   const size_t smem = sizeof(float) * (2 * TOR_MAX_K) * (2 * TOR_MAX_K);
   cudaFuncSetAttribute(k_bounds_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_bounds_batch<<<n, BOUNDS_THREADS, smem, s>>>(O, k, ld, layout, tol, out);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_bounds_patterns(const double *Ofull, int M, int ld, const unsigned long long *patterns, int words,
+                           int n, double tol, tor_bound *out, cudaStream_t s) {
+  const size_t smem = sizeof(float) * (2 * TOR_MAX_K) * (2 * TOR_MAX_K);
+  cudaFuncSetAttribute(k_bounds_patterns, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_bounds_patterns<<<n, BOUNDS_THREADS, smem, s>>>(Ofull, M, ld, patterns, words, tol, out);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

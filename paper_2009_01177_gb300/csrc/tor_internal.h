@@ -30,13 +30,27 @@ struct BatchPlan {
   tor_result *result;             // n: last finalized results (input of the AUTO round)
 };
 
+// what a batch walks: per-instance matrices, or click patterns of one full matrix
+struct BatchInput {
+  const double *const *O;              // instance mode: n matrices (2k_i x 2k_i, `layout`)
+  const int *k;                        // n click counts (pattern mode: popcounts, filled by the library)
+  const int *ld;                       // instance mode: n leading dimensions
+  int layout;
+  const double *Ofull;                 // pattern mode: full 2M x 2M O, xxpp, leading dim ldfull
+  const unsigned long long *patterns;  // pattern mode: n x words bitsets (bit j = mode j clicked)
+  int M, ldfull, words;                // words == 0 selects instance mode
+};
+
 int launch_batch_plan(const int *k, const tor_bound *bounds, int n, int prec, int kmax,
                       const unsigned char *r1_table, int mode, double tol, const BatchPlan &p, cudaStream_t s);
-int launch_batch_walk(int tier, int grid, int block, const double *const *O, const int *k, const int *ld,
-                      int layout, const BatchPlan &p, double *scratch, cudaStream_t s);
+int launch_batch_walk(int tier, int grid, int block, const BatchInput &in, const BatchPlan &p, double *scratch,
+                      cudaStream_t s);
+int launch_pattern_popcount(const unsigned long long *patterns, int n, int words, int *k, cudaStream_t s);
+int launch_bounds_patterns(const double *Ofull, int M, int ld, const unsigned long long *patterns, int words,
+                           int n, double tol, tor_bound *out, cudaStream_t s);
 int launch_batch_finalize(const int *k, int n, int only_escalated, double tol, const BatchPlan &p,
                           tor_result *out, cudaStream_t s);
-int batch_walk_max_blocks_per_sm(int tier, int block);
+int batch_walk_max_blocks_per_sm(int tier, int block, bool patterns);
 
 void launch_prep(const double *O, int k, int ld, int layout, double *B, double *Blo, cudaStream_t s);
 void launch_dfs(int tier, int grid, int block, const double *B, const double *Blo, int k, int r1,
@@ -52,6 +66,12 @@ int launch_bounds_batch(const double *const *O, const int *k, const int *ld, int
                         tor_bound *out, cudaStream_t s);
 int launch_bounds_single(const double *O, int k, int ld, int layout, double tol, tor_bound *out,
                          cudaStream_t s);
+int launch_propose_plain(const double *marg, int M, int C, int words, unsigned long long seed,
+                         unsigned long long step, unsigned long long *prop, double *logq_prop, cudaStream_t s);
+int launch_accept(int C, int M, int words, double logdet_sigma, const tor_result *tr,
+                  const unsigned long long *prop, const double *logq_prop, unsigned long long *pat, double *logp,
+                  double *logq, int *accepted, unsigned long long seed, unsigned long long step, cudaStream_t s);
+int mlp_modes(const tor_mlp *m);
 // store a message for tor_last_error() on the calling thread; returns code
 int record_error(int code, const char *msg);
 

@@ -47,6 +47,32 @@ __device__ __forceinline__ dd SrcDirect::get<TierDD>(int row, int col) const {
   return row == col ? two_sum(1.0, -v) : dd{-v, 0.0};
 }
 
+// B = I - O_S entries for a click pattern S of the full M-mode matrix O (xxpp,
+// leading dim ld): local mode m is the m-th clicked mode gm[m], whose x and p
+// rows are gm[m] and M + gm[m] (the selection rule under Eq. 1)
+struct SrcPattern {
+  const double *__restrict__ O;
+  int M, ld;
+  const unsigned char *gm;
+  __device__ __forceinline__ double o(int row, int col) const {
+    const int gr = (row & 1) * M + gm[row >> 1];
+    const int gc = (col & 1) * M + gm[col >> 1];
+    return O[(size_t)gr * ld + gc];
+  }
+  template <class Tier>
+  __device__ __forceinline__ typename Tier::T get(int row, int col) const;
+};
+template <>
+__device__ __forceinline__ double SrcPattern::get<TierF64>(int row, int col) const {
+  const double v = o(row, col);
+  return row == col ? 1.0 - v : -v;
+}
+template <>
+__device__ __forceinline__ dd SrcPattern::get<TierDD>(int row, int col) const {
+  const double v = o(row, col);
+  return row == col ? two_sum(1.0, -v) : dd{-v, 0.0};
+}
+
 // One chunk: the subsets whose high modes r1..k-1 are fixed by the bits of c.
 // Root: gather B over the fixed modes then the low modes into the thread's
 // stack S and eliminate the fixed modes in place; then the depth-first walk.

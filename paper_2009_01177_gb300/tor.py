@@ -89,8 +89,20 @@ SIGNATURES = {
     "tor_batch": (_I, [_VP, _VP, _VP, _VP, _I, _I, _I, _D, _VP, _VP]),
     "tor_bounds": (_I, [_VP, _VP, _VP, _VP, _I, _I, _D, _VP, _VP]),
     "tor_batch_reserve": (_I, [_VP, _I, _I]),
+    "tor_batch_patterns": (_I, [_VP, _VP, _I, _I, _VP, _I, _I, _D, _VP, _VP]),
     "tor_fp64_peak": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "tor_single_noalloc": (_I, [_VP, _I, _I, _I, _I, _VP, _VP]),
+    "tor_mlp_create": (_I, [_VP, _I, _I, _U64, ctypes.POINTER(_VP)]),
+    "tor_mlp_destroy": (None, [_VP]),
+    "tor_mlp_num_params": (_I, [_VP]),
+    "tor_mlp_get_params": (_I, [_VP, ctypes.POINTER(ctypes.c_float), _I]),
+    "tor_mlp_set_params": (_I, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "tor_mlp_logq": (_I, [_VP, _VP, _I, _VP, _VP]),
+    "tor_mlp_logits": (_I, [_VP, _VP, _I, ctypes.POINTER(ctypes.c_float)]),
+    "tor_mlp_grad": (_I, [_VP, _VP, _VP, _I, ctypes.POINTER(ctypes.c_float), _VP]),
+    "tor_mlp_train_step": (_I, [_VP, _VP, _VP, _I, ctypes.c_float, ctypes.POINTER(ctypes.c_float), _VP]),
+    "tor_mlp_sample": (_I, [_VP, _I, _U64, _U64, _VP, _VP, _VP]),
+    "gbs_sample_step": (_I, [_VP, _VP, _I, _I, _D, _VP, _VP, _I, _VP, _VP, _VP, _VP, _U64, _U64, _I, _D, _VP]),
     "tor_set_timing": (_I, [_VP, _I]),
     "tor_walk_time": (_I, [_VP, ctypes.POINTER(ctypes.c_float)]),
 }
@@ -134,6 +146,17 @@ def _mat(O: torch.Tensor):
     if O.stride(1) != 1:
         raise ValueError("O must be row-major (unit column stride)")
     return O.shape[0] // 2, O.stride(0)
+
+
+def pack_patterns(patterns, M: int) -> torch.Tensor:
+    """(n, M) 0/1 array-like -> int64 tensor (n, ceil(M/64)) of bitsets (bit j = mode j)."""
+    import numpy as np
+    a = np.asarray(patterns, dtype=np.uint8).reshape(-1, M)
+    words = (M + 63) // 64
+    out = np.zeros((a.shape[0], words), dtype=np.uint64)
+    for j in range(M):
+        out[:, j // 64] |= a[:, j].astype(np.uint64) << np.uint64(j % 64)
+    return torch.from_numpy(out.view(np.int64))
 
 
 def results_from_tensor(out: torch.Tensor, n: int):
@@ -241,6 +264,38 @@ class Context:
         raw = out.cpu().numpy().tobytes()
         return [TorResult.from_bytes(raw[i * RESULT_BYTES:(i + 1) * RESULT_BYTES]) for i in range(n)]
 
+    def batch_patterns_async(self, Ofull: torch.Tensor, patterns: torch.Tensor, out: torch.Tensor,
+                             prec: str = "fp64", tol: float = 1e-10, stream=None):
+        """tor_batch_patterns: patterns is an int64 CUDA tensor (n, ceil(M/64)) of bitsets."""
+        k2, ld = _mat(Ofull)
+        n = patterns.shape[0]
+        if out.numel() < n * RESULT_BYTES:
+            raise ValueError("out too small")
+        _check(self.lib.tor_batch_patterns(self.h, Ofull.data_ptr(), k2, ld, patterns.data_ptr(), n,
+                                           _PREC[prec], tol, _stream(stream), out.data_ptr()))
+
+    def batch_patterns(self, Ofull: torch.Tensor, patterns, prec: str = "fp64", tol: float = 1e-10):
+        """Tor(O_S) for each 0/1 pattern (rows of a (n, M) array-like); blocking."""
+        M = Ofull.shape[0] // 2
+        bits = pack_patterns(patterns, M).to(Ofull.device)
+        n = bits.shape[0]
+        out = torch.zeros(n * RESULT_BYTES, dtype=torch.uint8, device=Ofull.device)
+        self.batch_patterns_async(Ofull, bits, out, prec=prec, tol=tol)
+        return results_from_tensor(out, n)
+
+    def sample_step(self, Ofull: torch.Tensor, logdet_sigma: float, patterns: torch.Tensor, logp: torch.Tensor,
+                    logq: torch.Tensor, accepted: torch.Tensor, seed: int, step: int, marg_p=None,
+                    proposal=None, prec: str = "fp64", tol: float = 1e-10, stream=None):
+        """gbs_sample_step on device state tensors (patterns int64 (C, W), logp/logq float64, accepted int32)."""
+        k2, ld = _mat(Ofull)
+        C = patterns.shape[0]
+        _check(self.lib.gbs_sample_step(self.h, Ofull.data_ptr(), k2, ld, float(logdet_sigma),
+                                        marg_p.data_ptr() if marg_p is not None else None,
+                                        proposal.h if proposal is not None else None, C, patterns.data_ptr(),
+                                        logp.data_ptr(), logq.data_ptr(), accepted.data_ptr(),
+                                        seed & 0xFFFFFFFFFFFFFFFF, step & 0xFFFFFFFFFFFFFFFF, _PREC[prec], tol,
+                                        _stream(stream)))
+
     def set_timing(self, on: bool):
         _check(self.lib.tor_set_timing(self.h, int(bool(on))))
 
@@ -286,6 +341,79 @@ def limbs_to_int(limbs4) -> int:
     if v >> 255:
         v -= 1 << 256
     return v
+
+
+class MLP:
+    """The MADE proposal network (tor_mlp_*): BF16 tensor-core forward/backward, FP32 Adam."""
+
+    def __init__(self, ctx: Context, M: int, hidden: int = 256, seed: int = 0):
+        self.lib = load_library()
+        self.M, self.H = M, hidden
+        self.words = (M + 63) // 64
+        h = ctypes.c_void_p()
+        _check(self.lib.tor_mlp_create(ctx.h, M, hidden, seed, ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tor_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_params(self) -> int:
+        return self.lib.tor_mlp_num_params(self.h)
+
+    def get_params(self, which: int = 0):
+        import numpy as np
+        out = np.zeros(self.num_params, dtype=np.float32)
+        _check(self.lib.tor_mlp_get_params(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), which))
+        return out
+
+    def set_params(self, theta):
+        import numpy as np
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        if a.size != self.num_params:
+            raise ValueError("wrong parameter count")
+        _check(self.lib.tor_mlp_set_params(self.h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def logq(self, patterns: torch.Tensor, stream=None) -> torch.Tensor:
+        B = patterns.shape[0]
+        out = torch.empty(B, dtype=torch.float64, device=patterns.device)
+        _check(self.lib.tor_mlp_logq(self.h, patterns.data_ptr(), B, out.data_ptr(), _stream(stream)))
+        return out
+
+    def logits(self, patterns: torch.Tensor):
+        import numpy as np
+        B = patterns.shape[0]
+        out = np.zeros((B, self.M), dtype=np.float32)
+        _check(self.lib.tor_mlp_logits(self.h, patterns.data_ptr(), B,
+                                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return out
+
+    def grad(self, patterns: torch.Tensor, w: torch.Tensor, stream=None) -> float:
+        loss = ctypes.c_float()
+        _check(self.lib.tor_mlp_grad(self.h, patterns.data_ptr(), w.data_ptr(), patterns.shape[0],
+                                     ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+    def train_step(self, patterns: torch.Tensor, w: torch.Tensor, lr: float = 1e-3, stream=None) -> float:
+        loss = ctypes.c_float()
+        _check(self.lib.tor_mlp_train_step(self.h, patterns.data_ptr(), w.data_ptr(), patterns.shape[0],
+                                           ctypes.c_float(lr), ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+    def sample(self, B: int, seed: int, step: int, device="cuda", stream=None):
+        pats = torch.zeros((B, self.words), dtype=torch.int64, device=device)
+        lq = torch.zeros(B, dtype=torch.float64, device=device)
+        _check(self.lib.tor_mlp_sample(self.h, B, seed & 0xFFFFFFFFFFFFFFFF, step & 0xFFFFFFFFFFFFFFFF,
+                                       pats.data_ptr(), lq.data_ptr(), _stream(stream)))
+        return pats, lq
 
 
 _default = None

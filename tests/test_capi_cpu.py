@@ -14,7 +14,7 @@ HEADER = os.path.join(ROOT, "include", "torontonian.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(tor_[a-z0-9_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b((?:tor|gbs)_[a-z0-9_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
@@ -26,8 +26,8 @@ def lib():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for required in ("tor_single", "tor_batch", "tor_bounds", "tor_create", "tor_destroy",
-                     "tor_last_error", "tor_chunks"):
+    for required in ("tor_single", "tor_batch", "tor_bounds", "gbs_sample_step", "tor_create",
+                     "tor_destroy", "tor_last_error", "tor_chunks"):
         assert required in names
 
 
