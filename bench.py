@@ -7,6 +7,8 @@ Haar U, eta = 0.3, seed 2), FP64 tier.  One step = one full Torontonian:
 prep (I - O, basis) + chunk roots + depth-first walk + exact reduction.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+  python bench.py --mode batch   # 4096 click patterns, one scheduled batch vs one launch each
+  python bench.py --mode mh      # MH sampling, learned vs plain proposal (M = 60; TV at M = 20)
 
 Prints one JSON line on rank 0.  Under torchrun (N > 1) each rank evaluates
 the Torontonian of its own click pattern of the same state (independent
@@ -151,6 +153,224 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def marginals(st):
+    """Exact single-mode click probabilities 1 - 1/sqrt(det Sigma_jj) (input side)."""
+    import math
+    M = st.M
+    return np.array([1.0 - 1.0 / math.sqrt(np.linalg.det(st.Sigma[np.ix_([j, M + j], [j, M + j])]))
+                     for j in range(M)])
+
+
+def batch_patterns_m100(n, seed=4, k_lo=8, k_hi=30):
+    """Click patterns of the M = 100 state: independent clicks with the exact
+    single-mode marginals, kept when k_lo <= k <= k_hi (a stand-in for the
+    chain-rule sampler's patterns; same state, same click-count range)."""
+    from paper_2009_01177_gb300 import gbs_inputs as gi
+    st = gi.lossy_gbs_state(100, 0.6, 1.2, 0.3, seed)
+    marg = marginals(st)
+    rng = np.random.default_rng(seed)
+    pats = []
+    while len(pats) < n:
+        x = (rng.random(st.M) < marg).astype(np.uint8)
+        if k_lo <= x.sum() <= k_hi:
+            pats.append(x)
+    return st, np.array(pats)
+
+
+def run_batch(args):
+    """Batched Tor/s for 4096 patterns (k in [8, 30]) against one launch per pattern."""
+    import torch
+    from paper_2009_01177_gb300 import gbs_inputs as gi
+    from paper_2009_01177_gb300 import tor
+    st, pats = batch_patterns_m100(args.n)
+    ks = pats.sum(1)
+    subsets = float((2.0 ** ks).sum())
+    ctx = tor.Context(0)
+    Od = torch.from_numpy(st.O).cuda()
+    P = tor.pack_patterns(pats, st.M).cuda()
+    out = torch.zeros(len(pats) * tor.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        ctx.batch_patterns_async(Od, P, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        e0.record()
+        for _ in range(args.steps):
+            ctx.batch_patterns_async(Od, P, out)
+        e1.record()
+        torch.cuda.synchronize()
+    tb = e0.elapsed_time(e1) / 1e3 / args.steps
+    res = tor.results_from_tensor(out, len(pats))
+    # the same Torontonians, one tor_single_async launch each (matrices formed beforehand)
+    mats = [torch.from_numpy(gi.select(st.O, np.nonzero(x)[0])).cuda() for x in pats]
+    o1 = torch.zeros(tor.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    ctx.single_async(mats[0], o1)
+    torch.cuda.synchronize()
+    e0.record()
+    for m in mats:
+        ctx.single_async(m, o1)
+    e1.record()
+    torch.cuda.synchronize()
+    ts = e0.elapsed_time(e1) / 1e3
+    line = {"metric": "batched Tor/s (4096 patterns, k in [8,30])", "value": len(pats) / tb, "unit": "Tor/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tb,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{len(pats)} click patterns of a synthetic M=100 lossy GBS state "
+                                   "(r~U[0.6,1.2], eta=0.3, seed 4): independent clicks with the exact "
+                                   "single-mode marginals, kept if 8 <= k <= 30", "k_mean": float(ks.mean()),
+                       "subsets": subsets, "tier": "fp64"},
+            "subset_dets_per_s": subsets / tb,
+            "one_launch_each": {"Tor/s": len(pats) / ts, "subset_dets_per_s": subsets / ts, "s": ts},
+            "speedup_vs_one_launch_each": ts / tb,
+            "statuses_ok": int(sum(r.status == 0 for r in res)),
+            "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def _click_counts(pat):
+    """Click count of each row of an int64 (C, words) bitset tensor."""
+    a = pat.cpu().numpy().view(np.uint8)
+    return np.unpackbits(a, axis=1).sum(1)
+
+
+def _ess_geyer(x):
+    """Mean over chains of the effective sample size of a (T, C) series (Geyer's
+    initial positive sequence estimator)."""
+    T, C = x.shape
+    x = x - x.mean(0)
+    var = (x * x).mean(0) + 1e-12
+    rho = np.stack([(x[:T - t] * x[t:]).mean(0) / var for t in range(T)])  # lags 0..T-1
+    tau = np.ones(C)
+    alive = np.ones(C, dtype=bool)
+    for t in range(1, T - 1, 2):
+        g = rho[t] + rho[t + 1]
+        alive &= g > 0
+        tau += np.where(alive, 2.0 * g, 0.0)
+    return float(np.mean(T / np.maximum(tau, 1.0)))
+
+
+def run_mh(args):
+    """Accepted samples/s and ESS/s, learned vs plain proposal, same chains and tier;
+    TV distance to all 2^20 exact probabilities at M = 20."""
+    import math
+    import torch
+    from paper_2009_01177_gb300 import gbs_inputs as gi
+    from paper_2009_01177_gb300 import tor
+    ctx = tor.Context(0)
+    C = args.n
+
+    def chains(st, C=C):
+        words = (st.M + 63) // 64
+        return dict(O=torch.from_numpy(st.O).cuda(), logdet=float(np.linalg.slogdet(st.Sigma)[1]),
+                    pat=torch.zeros((C, words), dtype=torch.int64, device="cuda"),
+                    logp=torch.full((C,), -math.inf, dtype=torch.float64, device="cuda"),
+                    logq=torch.zeros(C, dtype=torch.float64, device="cuda"),
+                    acc=torch.zeros(C, dtype=torch.int32, device="cuda"),
+                    marg=torch.tensor(marginals(st), dtype=torch.float64, device="cuda"))
+
+    def run(ch, steps, seed, prop=None, record=None, t0=0, k_cap=0):
+        acc = torch.zeros((), dtype=torch.float64, device="cuda")
+        for s_ in range(steps):
+            ctx.sample_step(ch["O"], ch["logdet"], ch["pat"], ch["logp"], ch["logq"], ch["acc"], seed, t0 + s_,
+                            marg_p=ch["marg"], proposal=prop, prec="fp64", k_cap=k_cap)
+            acc += ch["acc"].double().mean()
+            if record is not None:
+                record.append(ch["pat"].clone())
+        return float(acc) / steps
+
+    def train(net, pats, w, iters, batch, lr, val=None):
+        """Adam on the weighted NLL; with val, keep the parameters of best validation NLL."""
+        best, best_theta, nll0 = None, None, None
+        if val is not None:
+            nll0 = best = float(-net.logq(val).mean())
+            best_theta = net.get_params(0)
+        for it in range(iters):
+            idx = torch.randint(0, pats.shape[0], (batch,), device="cuda")
+            net.train_step(pats[idx].contiguous(), w[idx].contiguous(), lr=lr)
+            if val is not None and (it + 1) % 200 == 0:
+                v = float(-net.logq(val).mean())
+                if v < best:
+                    best, best_theta = v, net.get_params(0)
+        if val is not None:
+            net.set_params(best_theta)
+        return nll0, best
+
+    # M = 60: train on states of the plain exact chain, then race the two proposals
+    st = gi.lossy_gbs_state(60, 0.5, 1.0, 0.5, 6)
+    marg60 = marginals(st)
+    k_cap = int(round(marg60.sum() + 6 * np.sqrt((marg60 * (1 - marg60)).sum()) + 4))
+    ch = chains(st)
+    hist = []
+    run(ch, 60, 6, record=hist, k_cap=k_cap)
+    pool = torch.cat(hist[10:])
+    pool = pool[torch.randperm(pool.shape[0], device="cuda")]
+    nval = pool.shape[0] // 10
+    val, trn = pool[:nval].contiguous(), pool[nval:].contiguous()
+    net = tor.MLP(ctx, st.M, 256, seed=6)
+    net.set_marginals(marg60)                 # start at the plain proposal
+    nll_plain, nll_learned = train(net, trn, torch.ones(trn.shape[0], dtype=torch.float32, device="cuda"),
+                                   3000, 4096, 3e-4, val=val)
+    res = {}
+    steps = max(8, 4 * args.steps)
+    for name, prop in (("plain", None), ("learned", net)):
+        chn = chains(st)
+        run(chn, 3, 7, prop)
+        series = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        acc = run(chn, steps, 7, prop, record=series, t0=100)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        ess = _ess_geyer(np.stack([_click_counts(p) for p in series]).astype(float))
+        res[name] = {"acceptance": acc, "accepted_samples_per_s": acc * C * steps / el,
+                     "ess_per_s": ess * C / el, "ess_per_chain": ess, "s": el, "steps": steps}
+    out = {"metric": "accepted samples/s, learned vs plain proposal (M=60)", "unit": "samples/s",
+           "value": res["learned"]["accepted_samples_per_s"], "n_gpus": 1, "higher_is_better": True,
+           "dtype": "f64 Torontonians, bf16 network", "data": "synthetic", "plain": res["plain"],
+           "learned": res["learned"],
+           "speedup_accepted": res["learned"]["accepted_samples_per_s"] / res["plain"]["accepted_samples_per_s"],
+           "speedup_ess": res["learned"]["ess_per_s"] / max(res["plain"]["ess_per_s"], 1e-30),
+           "validation_nll": {"plain_proposal": nll_plain, "learned": nll_learned}, "k_cap": k_cap,
+           "mean_clicks": float(marg60.sum()),
+           "config": {"workload": f"M=60 synthetic lossy GBS state (r~U[0.5,1.0], eta=0.5, seed 6), {C} "
+                                  "independence-MH chains targeting p(S | k <= k_cap); MADE 60-256-256-256-60 started at the "
+                                  "plain proposal, trained (3000 Adam steps, batch 4096, best of held-out NLL) on "
+                                  "50 x C states of the plain exact chain"}}
+    # M = 20: all 2^20 exact probabilities, then TV of the pooled chain states
+    st20 = gi.lossy_gbs_state(20, 0.5, 1.0, 0.5, 5)
+    allx = ((np.arange(1 << 20)[:, None] >> np.arange(20)[None, :]) & 1).astype(np.uint8)
+    O20 = torch.from_numpy(st20.O).cuda()
+    P20 = tor.pack_patterns(allx, 20).cuda()
+    o20 = torch.zeros((1 << 20) * tor.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    ctx.batch_patterns_async(O20, P20, o20, prec="auto", tol=1e-6)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.batch_patterns_async(O20, P20, o20, prec="auto", tol=1e-6)
+    torch.cuda.synchronize()
+    t_exact = time.perf_counter() - t0
+    r20 = tor.results_array(o20, 1 << 20)
+    p20 = (r20["hi"] + r20["lo"]) * math.exp(-0.5 * np.linalg.slogdet(st20.Sigma)[1])
+    net20 = tor.MLP(ctx, 20, 256, seed=5)
+    net20.set_marginals(marginals(st20))
+    train(net20, P20, torch.tensor(np.maximum(p20, 0), dtype=torch.float32, device="cuda"), 1500, 8192, 1e-3)
+    tv = {}
+    C20 = 16 * C
+    for name, prop in (("plain", None), ("learned", net20)):
+        chn = chains(st20, C20)
+        run(chn, 20, 9, prop)
+        series = []
+        run(chn, 100, 9, prop, record=series, t0=20)
+        codes = np.concatenate([p[:, 0].cpu().numpy() for p in series])
+        freq = np.bincount(codes, minlength=1 << 20) / codes.size
+        tv[name] = 0.5 * float(np.abs(freq - p20).sum())
+    out["m20"] = {"tv_pooled_100_steps": tv, "chains": C20, "samples_pooled": 100 * C20, "exact_table_s": t_exact,
+                  "sum_p": float(p20.sum()), "subset_dets": 3 ** 20,
+                  "statuses_ok": int((r20["status"] == 0).sum())}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -160,12 +380,20 @@ def main():
     ap.add_argument("--k", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "mh"])
+    ap.add_argument("--n", type=int, default=4096, help="patterns (batch) or chains (mh)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
 
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.mode == "batch":
+        run_batch(args)
+        return
+    if args.mode == "mh":
+        run_mh(args)
         return
 
     import torch

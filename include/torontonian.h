@@ -203,7 +203,9 @@ int tor_batch(tor_ctx *ctx, const double *const *O, const int *k, const int *ld,
  *   patterns  dev  n x ceil(M/64) uint64 bitsets, bit j of word j/64 = mode j
  *             clicked (M <= 128; at most TOR_MAX_K clicks per pattern).
  *   out       dev  n results, Tor(O_S) of each pattern.  p(S) = Tor / sqrt(det Sigma).
- * Same scheduling, precision and workspace rules as tor_batch.
+ * Same scheduling and precision rules as tor_batch; the workspace is sized
+ * for k_max = min(M, TOR_MAX_K) (allocating only when n or that k_max grows),
+ * so every pattern of the state fits.
  */
 int tor_batch_patterns(tor_ctx *ctx, const double *O, int M, int ld, const uint64_t *patterns, int n,
                        int prec, double tol, cudaStream_t stream, tor_result *out);
@@ -253,6 +255,8 @@ int tor_mlp_num_params(const tor_mlp *m);
 /* which: 0 weights, 1 gradients of the last grad/train call, 2 the 0/1 masks */
 int tor_mlp_get_params(const tor_mlp *m, float *host, int which);
 int tor_mlp_set_params(tor_mlp *m, const float *host);   /* masked entries forced to 0 */
+/* start at the plain proposal: last layer 0, output biases logit(marg_host[j]) */
+int tor_mlp_set_marginals(tor_mlp *m, const double *marg_host);
 /* log q(x) for B patterns (dev bitsets, ceil(M/64) words each) -> dev doubles */
 int tor_mlp_logq(tor_mlp *m, const uint64_t *patterns, int B, double *logq, cudaStream_t stream);
 /* the M logits of each pattern, to host (B x M floats) */
@@ -287,12 +291,15 @@ int tor_mlp_sample(tor_mlp *m, int B, uint64_t seed, uint64_t step, uint64_t *pa
  *   seed, step    Philox4x32-10 key and counter: draw j of chain c is at
  *                 (seed; step, c, j), j < M for the proposal, j = M to accept.
  *   prec, tol     tier for the exact Torontonians, as for tor_batch.
+ *   k_cap         > 0: proposals with more than k_cap clicks are rejected without
+ *                 evaluating them (an exact Torontonian costs 2^k), so the chains
+ *                 target p(S | |S| <= k_cap); <= 0: no cap beyond TOR_MAX_K.
  * Asynchronous; the Torontonians use tor_batch_patterns' workspace rules.
  */
 int gbs_sample_step(tor_ctx *ctx, const double *O, int M, int ld, double logdet_sigma,
                     const double *marg_p, tor_mlp *proposal, int C, uint64_t *patterns,
                     double *logp, double *logq, int *accepted, uint64_t seed, uint64_t step,
-                    int prec, double tol, cudaStream_t stream);
+                    int prec, double tol, int k_cap, cudaStream_t stream);
 
 /* -------------------------------------------------------------- utilities */
 
@@ -303,6 +310,20 @@ int tor_set_timing(tor_ctx *ctx, int on);
 /* Duration in ms of the walk kernel of the most recent timed call (waits for
  * that kernel to finish).  TOR_EINVAL if no timed call was made. */
 int tor_walk_time(tor_ctx *ctx, float *ms);
+
+/*
+ * tor_autotune: pick the chunk depth d (walked modes per chunk k - d) and
+ * blocks per SM that run fastest for instances of k clicks in tier `prec`,
+ * by timing candidates (k - d in {8, 10, 12, 14, 16}, 2-4 blocks per SM) on a
+ * synthetic instance of that size (the walk's cost depends only on k).  The
+ * choice is kept in the context (used by tor_single when chunk bits are
+ * automatic, and by the batch planner for that k) and, if cache_path is not
+ * NULL, appended to that file as one JSON object per line keyed by GPU name,
+ * k and tier; a matching cached line is reused without timing.  Synchronous;
+ * allocates a small instance.  k in [1, 40].
+ */
+int tor_autotune(tor_ctx *ctx, int k, int prec, const char *cache_path, int *chunk_bits_out,
+                 int *blocks_per_sm_out);
 
 /* Measured FP64 FMA throughput of this GPU (DFMA per second), from a
  * dependent-chain-free DFMA loop over all SMs; the roofline denominator. */

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <cstdint>
 #include <new>
+#include <cstdlib>
 #include "tor_internal.h"
 #include "tor_walk.cuh"
 
@@ -58,6 +59,9 @@ struct tor_ctx {
   int *k_dev = nullptr;  // pattern mode: click counts
   Buf mh;                // sampler: proposals, their log q, their Torontonians
   unsigned char r1_table[3][65];  // walked modes per chunk, by tier and k
+  // autotuned single-instance settings by tier and k (-1: not tuned)
+  signed char tuned_d[3][65];
+  signed char tuned_bps[3][65];
 };
 
 namespace {
@@ -81,8 +85,9 @@ int ensure(tor_ctx *c, Buf &b, size_t bytes) {
 }
 
 // chunk bits d (chunks fix the high d modes); r1 = k - d modes are walked per chunk
-int choose_chunk_bits(const tor_ctx *c, int k) {
+int choose_chunk_bits(const tor_ctx *c, int k, int tier = TOR_PREC_FP64) {
   if (c->chunk_bits >= 0) return c->chunk_bits < k ? c->chunk_bits : k;
+  if (k <= 64 && c->tuned_d[tier][k] >= 0) return c->tuned_d[tier][k];
   int d = k - 10;
   const int cap = (k >= 36) ? 20 : 18;
   if (d > cap) d = cap;
@@ -153,6 +158,8 @@ int tor_create(tor_ctx **out, int device) {
   tor_ctx *c = new (std::nothrow) tor_ctx();
   if (!c) return fail(TOR_ENOMEM, "host allocation failed");
   c->device = device;
+  memset(c->tuned_d, -1, sizeof(c->tuned_d));
+  memset(c->tuned_bps, -1, sizeof(c->tuned_bps));
   for (int kk = 0; kk <= 64; ++kk) {
     c->r1_table[0][kk] = 0;
     c->r1_table[TOR_PREC_FP64][kk] = (unsigned char)(kk < 14 ? kk : 14);
@@ -233,9 +240,13 @@ int tor_single_async(tor_ctx *ctx, const double *O, int k, int ld, int layout, i
     CK(cudaStreamSynchronize(s));  // `one` lives on this stack frame
     return TOR_OK;
   }
-  const int d = choose_chunk_bits(ctx, k);
+  const int d = choose_chunk_bits(ctx, k, prec);
   int grid = 0;
-  if ((rc = enqueue_walk(ctx, O, k, ld, layout, prec, d, 0ull, 1ull << d, nullptr, s, &grid))) return rc;
+  const int bps_saved = ctx->blocks_per_sm;
+  if (ctx->chunk_bits < 0 && ctx->tuned_bps[prec][k] > 0) ctx->blocks_per_sm = ctx->tuned_bps[prec][k];
+  rc = enqueue_walk(ctx, O, k, ld, layout, prec, d, 0ull, 1ull << d, nullptr, s, &grid);
+  ctx->blocks_per_sm = bps_saved;
+  if (rc) return rc;
   tor::launch_finalize((const unsigned long long *)ctx->block_part.p, grid, k, prec,
                        (const int *)ctx->status.p, out_dev, nullptr, s);
   CK(cudaGetLastError());
@@ -374,8 +385,9 @@ int tor_batch_reserve(tor_ctx *ctx, int n_max, int k_max) {
 }
 
 // enqueue bound pass (AUTO), plan, walks, finalize, and the AUTO second round
+// kcap < 0: instances up to the reserved k_max; else also refuse k > kcap (no work, TOR_EINVAL)
 static int batch_enqueue(tor_ctx *ctx, const tor::BatchInput &in, int n, int prec, double tol, cudaStream_t s,
-                         tor_result *out) {
+                         tor_result *out, int kcap = -1) {
   const tor::BatchPlan &p = ctx->plan;
   const bool pat = in.words > 0;
   const int block = ctx->threads_per_block;
@@ -388,7 +400,8 @@ static int batch_enqueue(tor_ctx *ctx, const tor::BatchInput &in, int n, int pre
     if (rc) return fail(TOR_ECUDA, "bound pass: %s", cudaGetErrorString(cudaGetLastError()));
     bd = ctx->bounds_dev;
   }
-  if (tor::launch_batch_plan(in.k, bd, n, prec, ctx->batch_kmax, ctx->r1_table_dev, 0, tol, p, s))
+  const int kmax = (kcap >= 0 && kcap < ctx->batch_kmax) ? kcap : ctx->batch_kmax;
+  if (tor::launch_batch_plan(in.k, bd, n, prec, kmax, ctx->r1_table_dev, 0, tol, p, s))
     return fail(TOR_ECUDA, "plan: %s", cudaGetErrorString(cudaGetLastError()));
   for (int tier = TOR_PREC_FP64; tier <= TOR_PREC_DD; ++tier) {
     if (prec != TOR_PREC_AUTO && prec != tier) continue;
@@ -398,7 +411,7 @@ static int batch_enqueue(tor_ctx *ctx, const tor::BatchInput &in, int n, int pre
   if (tor::launch_batch_finalize(in.k, n, 0, 0.0, p, out, s))
     return fail(TOR_ECUDA, "finalize: %s", cudaGetErrorString(cudaGetLastError()));
   if (prec == TOR_PREC_AUTO) {  // second round: FP64 results that miss tol are redone in double-double
-    if (tor::launch_batch_plan(in.k, bd, n, prec, ctx->batch_kmax, ctx->r1_table_dev, 1, tol, p, s) ||
+    if (tor::launch_batch_plan(in.k, bd, n, prec, kmax, ctx->r1_table_dev, 1, tol, p, s) ||
         tor::launch_batch_walk(TOR_PREC_DD, batch_grid(ctx, TOR_PREC_DD, pat), block, in, p, scratch, s) ||
         tor::launch_batch_finalize(in.k, n, 0, tol, p, out, s))
       return fail(TOR_ECUDA, "AUTO second round: %s", cudaGetErrorString(cudaGetLastError()));
@@ -443,8 +456,8 @@ int tor_batch(tor_ctx *ctx, const double *const *O, const int *k, const int *ld,
   return batch_enqueue(ctx, in, n, prec, tol, s, out);
 }
 
-int tor_batch_patterns(tor_ctx *ctx, const double *O, int M, int ld, const uint64_t *patterns, int n, int prec,
-                       double tol, cudaStream_t s, tor_result *out) {
+static int batch_patterns(tor_ctx *ctx, const double *O, int M, int ld, const uint64_t *patterns, int n, int prec,
+                          double tol, cudaStream_t s, tor_result *out, int kcap) {
   int rc = batch_check(ctx, n, prec, tol);
   if (rc) return rc;
   if (n == 0) return TOR_OK;
@@ -453,28 +466,28 @@ int tor_batch_patterns(tor_ctx *ctx, const double *O, int M, int ld, const uint6
   if (ld < 2 * M) return fail(TOR_EINVAL, "ld = %d < 2M = %d", ld, 2 * M);
   CK(cudaSetDevice(ctx->device));
   const int words = (M + 63) / 64;
-  if (n > ctx->batch_nmax || ctx->batch_kmax < 0) {
-    // the click counts must exist before sizing: a scratch count array first
-    Buf tmp;
-    if ((rc = ensure(ctx, tmp, sizeof(int) * (size_t)n))) return rc;
-    if (tor::launch_pattern_popcount((const unsigned long long *)patterns, n, words, (int *)tmp.p, s)) {
-      cudaFree(tmp.p);
-      return fail(TOR_ECUDA, "popcount: %s", cudaGetErrorString(cudaGetLastError()));
-    }
-    rc = batch_autoreserve(ctx, (const int *)tmp.p, n, s);
-    cudaFree(tmp.p);
-    if (rc) return rc;
-  }
+  // patterns of this state can have up to min(M, TOR_MAX_K) clicks: size for that
+  // once, so that no later pattern is refused for outgrowing an earlier batch
+  const int kstate = M < TOR_MAX_K ? M : TOR_MAX_K;
+  if (n > ctx->batch_nmax || ctx->batch_kmax < kstate)
+    if ((rc = tor_batch_reserve(ctx, n > ctx->batch_nmax ? n : ctx->batch_nmax,
+                                kstate > ctx->batch_kmax ? kstate : ctx->batch_kmax)))
+      return rc;
   if (tor::launch_pattern_popcount((const unsigned long long *)patterns, n, words, ctx->k_dev, s))
     return fail(TOR_ECUDA, "popcount: %s", cudaGetErrorString(cudaGetLastError()));
   tor::BatchInput in{nullptr, ctx->k_dev, nullptr, TOR_LAYOUT_XXPP, O, (const unsigned long long *)patterns, M, ld,
                      words};
-  return batch_enqueue(ctx, in, n, prec, tol, s, out);
+  return batch_enqueue(ctx, in, n, prec, tol, s, out, kcap);
+}
+
+int tor_batch_patterns(tor_ctx *ctx, const double *O, int M, int ld, const uint64_t *patterns, int n, int prec,
+                       double tol, cudaStream_t s, tor_result *out) {
+  return batch_patterns(ctx, O, M, ld, patterns, n, prec, tol, s, out, -1);
 }
 
 int gbs_sample_step(tor_ctx *ctx, const double *O, int M, int ld, double logdet_sigma, const double *marg_p,
                     tor_mlp *proposal, int C, uint64_t *patterns, double *logp, double *logq, int *accepted,
-                    uint64_t seed, uint64_t step, int prec, double tol, cudaStream_t s) {
+                    uint64_t seed, uint64_t step, int prec, double tol, int k_cap, cudaStream_t s) {
   if (!ctx) return fail(TOR_EINVAL, "null context");
   if (M < 1 || M > 128) return fail(TOR_EINVAL, "M = %d outside [1, 128]", M);
   if (C < 0) return fail(TOR_EINVAL, "C = %d < 0", C);
@@ -498,7 +511,8 @@ int gbs_sample_step(tor_ctx *ctx, const double *O, int M, int ld, double logdet_
   } else if (tor::launch_propose_plain(marg_p, M, C, words, seed, step, prop, lq_prop, s)) {
     return fail(TOR_ECUDA, "proposal: %s", cudaGetErrorString(cudaGetLastError()));
   }
-  if ((rc = tor_batch_patterns(ctx, O, M, ld, (const uint64_t *)prop, C, prec, tol, s, res))) return rc;
+  if ((rc = batch_patterns(ctx, O, M, ld, (const uint64_t *)prop, C, prec, tol, s, res, k_cap > 0 ? k_cap : -1)))
+    return rc;
   if (tor::launch_accept(C, M, words, logdet_sigma, res, prop, lq_prop, (unsigned long long *)patterns, logp, logq,
                          accepted, seed, step, s))
     return fail(TOR_ECUDA, "accept: %s", cudaGetErrorString(cudaGetLastError()));
@@ -516,6 +530,141 @@ int tor_bounds(tor_ctx *ctx, const double *const *O, const int *k, const int *ld
   CK(cudaSetDevice(ctx->device));
   if (tor::launch_bounds_batch(O, k, ld, n, layout, tol, out, s))
     return fail(TOR_ECUDA, "bound pass launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+  return TOR_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+namespace {
+
+struct TuneEntry {
+  char gpu[128];
+  int k, tier, d, bps;
+  double ms;
+};
+
+bool parse_line(const char *line, TuneEntry &e) {
+  // {"gpu": "...", "k": K, "tier": T, "chunk_bits": D, "blocks_per_sm": B, "ms": X}
+  const char *g = strstr(line, "\"gpu\": \"");
+  if (!g) return false;
+  g += 8;
+  const char *ge = strchr(g, '"');
+  if (!ge || ge - g >= (long)sizeof(e.gpu)) return false;
+  memcpy(e.gpu, g, ge - g);
+  e.gpu[ge - g] = 0;
+  const char *kk = strstr(line, "\"k\": "), *t = strstr(line, "\"tier\": "),
+             *d = strstr(line, "\"chunk_bits\": "), *b = strstr(line, "\"blocks_per_sm\": "),
+             *m = strstr(line, "\"ms\": ");
+  if (!kk || !t || !d || !b || !m) return false;
+  e.k = atoi(kk + 5);
+  e.tier = atoi(t + 8);
+  e.d = atoi(d + 14);
+  e.bps = atoi(b + 17);
+  e.ms = atof(m + 6);
+  return e.k >= 0 && e.k <= 64 && (e.tier == TOR_PREC_FP64 || e.tier == TOR_PREC_DD) && e.d >= 0 && e.d <= e.k &&
+         e.bps >= 1 && e.bps <= 16;
+}
+
+}  // namespace
+
+int tor_autotune(tor_ctx *ctx, int k, int prec, const char *cache_path, int *chunk_bits_out,
+                 int *blocks_per_sm_out) {
+  if (!ctx) return fail(TOR_EINVAL, "null context");
+  if (k < 1 || k > 40) return fail(TOR_EINVAL, "autotune k = %d outside [1, 40]", k);
+  if (prec != TOR_PREC_FP64 && prec != TOR_PREC_DD) return fail(TOR_EINVAL, "prec must be FP64 or DD");
+  CK(cudaSetDevice(ctx->device));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, ctx->device));
+  // 1. a cached result for this GPU, k and tier
+  if (cache_path) {
+    FILE *f = fopen(cache_path, "r");
+    if (f) {
+      char line[512];
+      TuneEntry e, best{};
+      bool found = false;
+      while (fgets(line, sizeof(line), f))
+        if (parse_line(line, e) && e.k == k && e.tier == prec && strcmp(e.gpu, prop.name) == 0) {
+          best = e;
+          found = true;
+        }
+      fclose(f);
+      if (found) {
+        ctx->tuned_d[prec][k] = (signed char)best.d;
+        ctx->tuned_bps[prec][k] = (signed char)best.bps;
+        ctx->r1_table[prec][k] = (unsigned char)(k - best.d);
+        if (chunk_bits_out) *chunk_bits_out = best.d;
+        if (blocks_per_sm_out) *blocks_per_sm_out = best.bps;
+        return TOR_OK;
+      }
+    }
+  }
+  // 2. time the candidates on a synthetic instance (O = I/4: same work as any
+  //    positive definite input of this size, which is all the walk's cost depends on)
+  const int n = 2 * k;
+  double *O = nullptr;
+  tor_result *res = nullptr;
+  if (cudaMalloc(&O, sizeof(double) * n * n) != cudaSuccess || cudaMalloc(&res, sizeof(tor_result)) != cudaSuccess) {
+    cudaFree(O);
+    return fail(TOR_ENOMEM, "autotune allocation failed");
+  }
+  double *h = new (std::nothrow) double[(size_t)n * n];
+  if (!h) { cudaFree(O); cudaFree(res); return fail(TOR_ENOMEM, "host allocation failed"); }
+  for (int i = 0; i < n * n; ++i) h[i] = (i / n == i % n) ? 0.25 : 0.0;
+  cudaMemcpy(O, h, sizeof(double) * n * n, cudaMemcpyHostToDevice);
+  delete[] h;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int saved_d = ctx->chunk_bits, saved_bps = ctx->blocks_per_sm;
+  double best_ms = 1e30;
+  int best_d = choose_chunk_bits(ctx, k), best_bps = saved_bps;
+  const int r1s[] = {8, 10, 12, 14, 16};
+  const int bpss[] = {2, 3, 4};
+  int rc = TOR_OK;
+  for (int r1 : r1s) {
+    if (r1 > k) continue;
+    const int d = k - r1;
+    if (d > 24) continue;
+    for (int bps : bpss) {
+      ctx->chunk_bits = d;
+      ctx->blocks_per_sm = bps;
+      if ((rc = tor_single_async(ctx, O, k, n, TOR_LAYOUT_XXPP, prec, 0, res))) break;  // warm-up, sizes workspace
+      cudaEventRecord(e0, 0);
+      for (int r = 0; r < 2 && rc == TOR_OK; ++r) rc = tor_single_async(ctx, O, k, n, TOR_LAYOUT_XXPP, prec, 0, res);
+      cudaEventRecord(e1, 0);
+      if (rc) break;
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms / 2 < best_ms) {
+        best_ms = ms / 2;
+        best_d = d;
+        best_bps = bps;
+      }
+    }
+    if (rc) break;
+  }
+  ctx->chunk_bits = saved_d;
+  ctx->blocks_per_sm = saved_bps;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(O);
+  cudaFree(res);
+  if (rc) return rc;
+  ctx->tuned_d[prec][k] = (signed char)best_d;
+  ctx->tuned_bps[prec][k] = (signed char)best_bps;
+  ctx->r1_table[prec][k] = (unsigned char)(k - best_d);
+  if (ctx->r1_table_dev)
+    CK(cudaMemcpy(ctx->r1_table_dev, ctx->r1_table, sizeof(ctx->r1_table), cudaMemcpyHostToDevice));
+  if (cache_path) {
+    FILE *f = fopen(cache_path, "a");
+    if (f) {
+      fprintf(f, "{\"gpu\": \"%s\", \"k\": %d, \"tier\": %d, \"chunk_bits\": %d, \"blocks_per_sm\": %d, \"ms\": %.4f}\n",
+              prop.name, k, prec, best_d, best_bps, best_ms);
+      fclose(f);
+    }
+  }
+  if (chunk_bits_out) *chunk_bits_out = best_d;
+  if (blocks_per_sm_out) *blocks_per_sm_out = best_bps;
   return TOR_OK;
 }
 

@@ -153,6 +153,8 @@ k_batch_plan(const int *__restrict__ k, const tor_bound *__restrict__ bounds, in
 template <class Tier, bool PAT>
 __global__ void __launch_bounds__(128)
 k_batch_walk(BatchInput in, BatchPlan p, double *__restrict__ scratch) {
+  extern __shared__ double smem[];
+  double *Q = smem + threadIdx.x;
   constexpr int t = (Tier::W == 1) ? 0 : 1;
   const size_t st = (size_t)gridDim.x * blockDim.x;
   const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -188,10 +190,10 @@ k_batch_walk(BatchInput in, BatchPlan p, double *__restrict__ scratch) {
           for (unsigned long long bits = in.patterns[(size_t)i * in.words + w]; bits && m < 64; bits &= bits - 1)
             gm[m++] = (unsigned char)(64 * w + __ffsll((long long)bits) - 1);
         const SrcPattern src{in.Ofull, in.M, in.ldfull, gm};
-        walk_chunk<Tier>(src, ki, r1, c, S, st, Sm);
+        walk_chunk<Tier>(src, ki, r1, c, S, st, Sm, Q, blockDim.x);
       } else {
         const SrcDirect src{in.O[i], ki, in.ld[i], in.layout};
-        walk_chunk<Tier>(src, ki, r1, c, S, st, Sm);
+        walk_chunk<Tier>(src, ki, r1, c, S, st, Sm, Q, blockDim.x);
       }
       fx_atomic_add(p.acc + (size_t)i * 8, Sm.tor);
       fx_atomic_add(p.acc + (size_t)i * 8 + 4, Sm.sabs);
@@ -228,11 +230,13 @@ int launch_batch_walk(int tier, int grid, int block, const BatchInput &in, const
                       cudaStream_t s) {
   const bool pat = in.words > 0;
   if (tier == TOR_PREC_DD) {
-    if (pat) k_batch_walk<TierDD, true><<<grid, block, 0, s>>>(in, p, scratch);
-    else k_batch_walk<TierDD, false><<<grid, block, 0, s>>>(in, p, scratch);
+    const size_t sm = walk_smem_bytes<TierDD>(block);
+    if (pat) k_batch_walk<TierDD, true><<<grid, block, sm, s>>>(in, p, scratch);
+    else k_batch_walk<TierDD, false><<<grid, block, sm, s>>>(in, p, scratch);
   } else {
-    if (pat) k_batch_walk<TierF64, true><<<grid, block, 0, s>>>(in, p, scratch);
-    else k_batch_walk<TierF64, false><<<grid, block, 0, s>>>(in, p, scratch);
+    const size_t sm = walk_smem_bytes<TierF64>(block);
+    if (pat) k_batch_walk<TierF64, true><<<grid, block, sm, s>>>(in, p, scratch);
+    else k_batch_walk<TierF64, false><<<grid, block, sm, s>>>(in, p, scratch);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -257,16 +261,21 @@ int launch_batch_finalize(const int *k, int n, int only_escalated, double tol, c
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int batch_walk_max_blocks_per_sm(int tier, int block, bool patterns) {
+template <class K>
+static int occ_of(K kern, int block, size_t sm) {
   int nb = 0;
-  cudaError_t e;
-  if (tier == TOR_PREC_DD)
-    e = patterns ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_walk<TierDD, true>, block, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_walk<TierDD, false>, block, 0);
-  else
-    e = patterns ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_walk<TierF64, true>, block, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_walk<TierF64, false>, block, 0);
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, block, sm);
   return (e == cudaSuccess && nb > 0) ? nb : 1;
+}
+
+int batch_walk_max_blocks_per_sm(int tier, int block, bool patterns) {
+  if (tier == TOR_PREC_DD) {
+    const size_t sm = walk_smem_bytes<TierDD>(block);
+    return patterns ? occ_of(k_batch_walk<TierDD, true>, block, sm) : occ_of(k_batch_walk<TierDD, false>, block, sm);
+  }
+  const size_t sm = walk_smem_bytes<TierF64>(block);
+  return patterns ? occ_of(k_batch_walk<TierF64, true>, block, sm) : occ_of(k_batch_walk<TierF64, false>, block, sm);
 }
 
 }  // namespace tor

@@ -90,6 +90,15 @@ __device__ __forceinline__ void fx_add_signed(Fx256 &acc, double x, bool neg, in
 #ifndef TOR_RSQRT_DF
 #define TOR_RSQRT_DF 0
 #endif
+// Nodes of at most RSMEM modes live in one shared-memory slot per thread.  A
+// node of r <= RREG + 2 modes has only register-resident children and its
+// last child, which it overwrites in place, so one slot is enough.
+#ifndef TOR_F64_RSMEM
+#define TOR_F64_RSMEM 5
+#endif
+#ifndef TOR_DD_RSMEM
+#define TOR_DD_RSMEM 4
+#endif
 
 __device__ __forceinline__ double dmul(double a, double b) { return a * b; }
 
@@ -146,6 +155,7 @@ struct TierF64 {
   static constexpr int W = 1;      // doubles per stored entry
   static constexpr int RREG = TOR_F64_RREG;       // register-resident subtree size (modes)
   static constexpr int RUNROLL = TOR_F64_RUNROLL; // memory-tier updates unrolled up to this child size
+  static constexpr int RSMEM = TOR_F64_RSMEM;     // shared-memory node size (modes), <= RREG + 2
 
   __device__ static __forceinline__ T ld(const double *P, int e, size_t st) { return P[(size_t)e * st]; }
   __device__ static __forceinline__ void stv(double *P, int e, size_t st, T v) { P[(size_t)e * st] = v; }
@@ -183,6 +193,7 @@ struct TierDD {
   static constexpr int W = 2;
   static constexpr int RREG = 2;
   static constexpr int RUNROLL = 4;
+  static constexpr int RSMEM = TOR_DD_RSMEM;
 
   __device__ static __forceinline__ T ld(const double *P, int e, size_t st) {
     return {P[(size_t)(2 * e) * st], P[(size_t)(2 * e + 1) * st]};
@@ -292,7 +303,7 @@ __device__ __forceinline__ void mem_to_reg_child(int rp, const double *P, size_t
 // child C (size rp) = parent P's trailing block minus the rank-2 term; C may equal P.
 // Looped form, for children larger than Tier::RUNROLL modes (rare).
 template <class Tier>
-__device__ __noinline__ void schur_mem_loop(const double *P, double *C, size_t st, int rp,
+__device__ __noinline__ void schur_mem_loop(const double *P, size_t sp, double *C, size_t sc, int rp,
                                             typename Tier::T a, typename Tier::T b,
                                             typename Tier::T d, typename Tier::T y) {
   using T = typename Tier::T;
@@ -301,14 +312,14 @@ __device__ __noinline__ void schur_mem_loop(const double *P, double *C, size_t s
   const int n2 = 2 * rp;
   const int cx = ix(2 * rp + 1, 0), cp = ix(2 * rp, 0);
   for (int i = 0; i < n2; ++i) {
-    const T uxi = Tier::ld(P, cx + i, st), upi = Tier::ld(P, cp + i, st);
+    const T uxi = Tier::ld(P, cx + i, sp), upi = Tier::ld(P, cp + i, sp);
     T vx, vp;
     Tier::vrow(al, be, de, uxi, upi, vx, vp);
     const int row = ix(i, 0);
 #pragma unroll 4
     for (int j = 0; j <= i; ++j) {
-      const T s = Tier::ld(P, row + j, st);
-      Tier::stv(C, row + j, st, Tier::upd(s, vx, Tier::ld(P, cx + j, st), vp, Tier::ld(P, cp + j, st)));
+      const T s = Tier::ld(P, row + j, sp);
+      Tier::stv(C, row + j, sc, Tier::upd(s, vx, Tier::ld(P, cx + j, sp), vp, Tier::ld(P, cp + j, sp)));
     }
   }
 }
@@ -319,8 +330,8 @@ __device__ __noinline__ void schur_mem_loop(const double *P, double *C, size_t s
 // is written and never read again, so no reordering of independent accesses
 // can change the result, which is what the restrict qualifiers allow.
 template <class Tier, int RP>
-__device__ __forceinline__ void schur_mem_fixed(const double *__restrict__ P, double *__restrict__ C,
-                                                size_t st, typename Tier::T a, typename Tier::T b,
+__device__ __forceinline__ void schur_mem_fixed(const double *__restrict__ P, size_t sp, double *__restrict__ C,
+                                                size_t sc, typename Tier::T a, typename Tier::T b,
                                                 typename Tier::T d, typename Tier::T y) {
   using T = typename Tier::T;
   T al, be, de;
@@ -328,8 +339,8 @@ __device__ __forceinline__ void schur_mem_fixed(const double *__restrict__ P, do
   T ux[2 * RP], up[2 * RP];
 #pragma unroll
   for (int i = 0; i < 2 * RP; ++i) {
-    ux[i] = Tier::ld(P, ix(2 * RP + 1, i), st);
-    up[i] = Tier::ld(P, ix(2 * RP, i), st);
+    ux[i] = Tier::ld(P, ix(2 * RP + 1, i), sp);
+    up[i] = Tier::ld(P, ix(2 * RP, i), sp);
   }
 #pragma unroll
   for (int i = 0; i < 2 * RP; ++i) {
@@ -337,29 +348,30 @@ __device__ __forceinline__ void schur_mem_fixed(const double *__restrict__ P, do
     Tier::vrow(al, be, de, ux[i], up[i], vx, vp);
 #pragma unroll
     for (int j = 0; j <= i; ++j)
-      Tier::stv(C, ix(i, j), st, Tier::upd(Tier::ld(P, ix(i, j), st), vx, ux[j], vp, up[j]));
+      Tier::stv(C, ix(i, j), sc, Tier::upd(Tier::ld(P, ix(i, j), sp), vx, ux[j], vp, up[j]));
   }
 }
 
 template <class Tier, int RP>
-__device__ __forceinline__ bool schur_try(int rp, const double *P, double *C, size_t st,
+__device__ __forceinline__ bool schur_try(int rp, const double *P, size_t sp, double *C, size_t sc,
                                           typename Tier::T a, typename Tier::T b,
                                           typename Tier::T d, typename Tier::T y) {
   if constexpr (RP > Tier::RUNROLL) {
     return false;
   } else {
-    if (rp == RP) { schur_mem_fixed<Tier, RP>(P, C, st, a, b, d, y); return true; }
-    return schur_try<Tier, RP + 1>(rp, P, C, st, a, b, d, y);
+    if (rp == RP) { schur_mem_fixed<Tier, RP>(P, sp, C, sc, a, b, d, y); return true; }
+    return schur_try<Tier, RP + 1>(rp, P, sp, C, sc, a, b, d, y);
   }
 }
 
 // one out-of-line copy of the dispatch, so the unrolled bodies exist once in
 // the binary however many call sites there are (instruction-cache footprint)
 template <class Tier>
-__device__ __noinline__ void schur_mem(const double *P, double *C, size_t st, int rp,
+__device__ __noinline__ void schur_mem(const double *P, size_t sp, double *C, size_t sc, int rp,
                                        typename Tier::T a, typename Tier::T b,
                                        typename Tier::T d, typename Tier::T y) {
-  if (!schur_try<Tier, Tier::RREG + 1>(rp, P, C, st, a, b, d, y)) schur_mem_loop<Tier>(P, C, st, rp, a, b, d, y);
+  if (!schur_try<Tier, Tier::RREG + 1>(rp, P, sp, C, sc, a, b, d, y))
+    schur_mem_loop<Tier>(P, sp, C, sc, rp, a, b, d, y);
 }
 
 // per-thread stack extent (in entries) of a walk over r modes
@@ -372,20 +384,25 @@ __host__ __device__ constexpr int stack_entries(int r, int rreg) {
 // ------------------------------------------------------------ the walk
 // Visit every non-empty extension of the node stored at S (r modes, term t,
 // |Z| = par) in depth-first order; the node's own term is added by the caller.
+// Q/sq: this thread's shared-memory slot (Tier::RSMEM nodes; may be null to
+// keep every node in global memory).
 template <class Tier>
-__device__ void dfs_walk(double *S, size_t st, int r, typename Tier::T t, int par, int k, Sums &Sm) {
+__device__ void dfs_walk(double *S, size_t st, int r, typename Tier::T t, int par, int k, Sums &Sm,
+                         double *Q = nullptr, size_t sq = 0) {
   using T = typename Tier::T;
   struct Frame { int off, r, rp, par; T t; };
   Frame stk[33];
   int sp = 0;
   int off = 0, rp = 0;
+  bool insm = false;  // the current node lives in the shared-memory slot
   while (true) {
     if (rp < r) {
       const int cur = rp++;
-      const double *P = S + (size_t)(off * Tier::W) * st;
-      const T a = Tier::ld(P, ix(2 * cur + 1, 2 * cur + 1), st);
-      const T b = Tier::ld(P, ix(2 * cur + 1, 2 * cur), st);
-      const T d = Tier::ld(P, ix(2 * cur, 2 * cur), st);
+      const double *P = insm ? Q : S + (size_t)(off * Tier::W) * st;
+      const size_t ps = insm ? sq : st;
+      const T a = Tier::ld(P, ix(2 * cur + 1, 2 * cur + 1), ps);
+      const T b = Tier::ld(P, ix(2 * cur + 1, 2 * cur), ps);
+      const T d = Tier::ld(P, ix(2 * cur, 2 * cur), ps);
       const T det2 = Tier::det2(a, b, d);
       if (Tier::bad(det2) || Tier::bad(a)) Sm.flags |= ST_NOTPD;
       const T y = Tier::rsqrt(det2);
@@ -393,24 +410,39 @@ __device__ void dfs_walk(double *S, size_t st, int r, typename Tier::T t, int pa
       Tier::acc(Sm, tc, ((k ^ (par + 1)) & 1) != 0);
       if (cur == 0) continue;
       if (cur <= Tier::RREG) {
-        mem_to_reg_child<Tier>(cur, P, st, a, b, d, y, tc, par + 1, k, Sm);
+        mem_to_reg_child<Tier>(cur, P, ps, a, b, d, y, tc, par + 1, k, Sm);
+        continue;
+      }
+      if (Q && cur <= Tier::RSMEM) {  // into the shared-memory slot (in place when already there)
+        schur_mem<Tier>(P, ps, Q, sq, cur, a, b, d, y);
+        if (!insm && cur != r - 1) stk[sp++] = Frame{off, r, rp, par, t};
+        insm = true; r = cur; rp = 0; t = tc; par = par + 1;
         continue;
       }
       if (cur == r - 1) {  // last child: in place, the node is finished afterwards
-        schur_mem<Tier>(P, const_cast<double *>(P), st, cur, a, b, d, y);
+        schur_mem<Tier>(P, st, const_cast<double *>(P), st, cur, a, b, d, y);
         r = cur; rp = 0; t = tc; par = par + 1;
         continue;
       }
       const int coff = off + sz(r);
-      schur_mem<Tier>(P, S + (size_t)(coff * Tier::W) * st, st, cur, a, b, d, y);
+      schur_mem<Tier>(P, st, S + (size_t)(coff * Tier::W) * st, st, cur, a, b, d, y);
       stk[sp++] = Frame{off, r, rp, par, t};
       off = coff; r = cur; rp = 0; t = tc; par = par + 1;
     } else {
       if (sp == 0) break;
       --sp;
       off = stk[sp].off; r = stk[sp].r; rp = stk[sp].rp; par = stk[sp].par; t = stk[sp].t;
+      insm = false;
     }
   }
+}
+
+// shared-memory bytes a walk kernel needs per block: the per-thread slots, and
+// at least the 64 bytes per thread of the block's partial-sum reduction
+template <class Tier>
+__host__ __device__ constexpr size_t walk_smem_bytes(int threads) {
+  const size_t slot = (size_t)sz(Tier::RSMEM) * Tier::W * sizeof(double);
+  return (slot > 64 ? slot : 64) * (size_t)threads;
 }
 
 }  // namespace tor

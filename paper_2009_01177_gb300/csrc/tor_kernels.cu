@@ -42,9 +42,11 @@ k_dfs(const double *__restrict__ B, const double *__restrict__ Blo, int k, int r
       unsigned long long c_begin, unsigned long long c_end, double *__restrict__ scratch,
       unsigned long long *__restrict__ block_part, unsigned long long *__restrict__ chunk_part,
       int *__restrict__ status) {
+  extern __shared__ double smem[];
   const size_t st = (size_t)gridDim.x * blockDim.x;
   const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   double *S = scratch + gtid;
+  double *Q = smem + threadIdx.x;  // this thread's shared-memory node slot (stride blockDim.x)
   const SrcPrepped src{B, Blo, 2 * k};
 
   Fx256 tot_tor, tot_sabs;
@@ -57,7 +59,7 @@ k_dfs(const double *__restrict__ B, const double *__restrict__ Blo, int k, int r
     fx_zero(Sm.tor);
     fx_zero(Sm.sabs);
     Sm.flags = 0;
-    walk_chunk<Tier>(src, k, r1, c, S, st, Sm);
+    walk_chunk<Tier>(src, k, r1, c, S, st, Sm, Q, blockDim.x);
     if (chunk_part) {
       unsigned long long *o = chunk_part + (size_t)(c - c_begin) * 8;
 #pragma unroll
@@ -68,8 +70,9 @@ k_dfs(const double *__restrict__ B, const double *__restrict__ Blo, int k, int r
     flags |= Sm.flags;
   }
 
-  // block reduction (exact, so the order does not matter)
-  __shared__ unsigned long long red[128][8];
+  // block reduction (exact, so the order does not matter) in the node slots' memory
+  __syncthreads();
+  unsigned long long(*red)[8] = reinterpret_cast<unsigned long long(*)[8]>(smem);
 #pragma unroll
   for (int i = 0; i < 4; ++i) { red[threadIdx.x][i] = tot_tor.w[i]; red[threadIdx.x][4 + i] = tot_sabs.w[i]; }
   if (flags) atomicOr(status, flags);
@@ -130,17 +133,29 @@ void launch_dfs(int tier, int grid, int block, const double *B, const double *Bl
                 unsigned long long c0, unsigned long long c1, double *scratch,
                 unsigned long long *block_part, unsigned long long *chunk_part, int *status,
                 cudaStream_t s) {
-  if (tier == TOR_PREC_DD)
-    k_dfs<TierDD><<<grid, block, 0, s>>>(B, Blo, k, r1, c0, c1, scratch, block_part, chunk_part, status);
-  else
-    k_dfs<TierF64><<<grid, block, 0, s>>>(B, Blo, k, r1, c0, c1, scratch, block_part, chunk_part, status);
+  if (tier == TOR_PREC_DD) {
+    const size_t sm = walk_smem_bytes<TierDD>(block);
+    cudaFuncSetAttribute(k_dfs<TierDD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_dfs<TierDD><<<grid, block, sm, s>>>(B, Blo, k, r1, c0, c1, scratch, block_part, chunk_part, status);
+  } else {
+    const size_t sm = walk_smem_bytes<TierF64>(block);
+    cudaFuncSetAttribute(k_dfs<TierF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_dfs<TierF64><<<grid, block, sm, s>>>(B, Blo, k, r1, c0, c1, scratch, block_part, chunk_part, status);
+  }
 }
 
 int dfs_max_blocks_per_sm(int tier, int block) {
   int n = 0;
-  cudaError_t e = (tier == TOR_PREC_DD)
-                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dfs<TierDD>, block, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dfs<TierF64>, block, 0);
+  cudaError_t e;
+  if (tier == TOR_PREC_DD) {
+    const size_t sm = walk_smem_bytes<TierDD>(block);
+    cudaFuncSetAttribute(k_dfs<TierDD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dfs<TierDD>, block, sm);
+  } else {
+    const size_t sm = walk_smem_bytes<TierF64>(block);
+    cudaFuncSetAttribute(k_dfs<TierF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dfs<TierF64>, block, sm);
+  }
   return (e == cudaSuccess && n > 0) ? n : 1;
 }
 

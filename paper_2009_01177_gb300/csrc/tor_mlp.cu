@@ -41,7 +41,9 @@ using bf16 = __nv_bfloat16;
 
 // ------------------------------------------------------------- GEMM (NT)
 // C[m, n] = sum_k A[m, k] B[n, k] (+ bias[n]) (relu) (* [aux[m,n] > 0]) with
-// A: rows x K (lda), B: cols x K (ldb), both BF16 with K a multiple of 16.
+// A: rows x K (lda), B: cols x K (ldb), both BF16, K and the leading
+// dimensions multiples of 8 (16-byte rows of 8 BF16); the K tail past a
+// multiple of 32 reads as zeros.
 struct GemmArgs {
   const bf16 *A; int lda;
   const bf16 *B; int ldb;
@@ -52,53 +54,88 @@ struct GemmArgs {
   float *Cf; bf16 *Cb; int ldc;  // one of the two outputs
 };
 
-__device__ __forceinline__ uint32_t ld2(const bf16 *p, int row, int nrows, int ld, int k) {
-  if (row >= nrows) return 0u;
-  return *reinterpret_cast<const uint32_t *>(p + (size_t)row * ld + k);
+// Block tile 64 x 64 over K steps of 32, staged in shared memory with 16-byte
+// loads; 4 warps each own a 32 x 32 tile = 2 x 4 mma.m16n8k16 accumulators.
+// Shared rows are padded to 40 BF16 (80 bytes): the fragment reads of a warp
+// (8 rows x 4 words) then fall in 32 distinct banks.
+constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+
+__device__ __forceinline__ uint4 ld16(const bf16 *p, int row, int nrows, int ld, int k, int K) {
+  if (row >= nrows || k >= K) return make_uint4(0u, 0u, 0u, 0u);
+  return *reinterpret_cast<const uint4 *>(p + (size_t)row * ld + k);
 }
 
 __global__ void __launch_bounds__(128) k_gemm_nt(GemmArgs g) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ __align__(16) bf16 As[GBM][GBK + GPAD];
+  __shared__ __align__(16) bf16 Bs[GBN][GBK + GPAD];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int gid = lane >> 2, tig = lane & 3;
-  const int row0 = blockIdx.y * 32 + (warp >> 1) * 16;
-  const int col0 = blockIdx.x * 32 + (warp & 1) * 16;
-  float c[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-  for (int k0 = 0; k0 < g.K; k0 += 16) {
-    const int ka = k0 + tig * 2;
-    const uint32_t a0 = ld2(g.A, row0 + gid, g.m, g.lda, ka);
-    const uint32_t a1 = ld2(g.A, row0 + gid + 8, g.m, g.lda, ka);
-    const uint32_t a2 = ld2(g.A, row0 + gid, g.m, g.lda, ka + 8);
-    const uint32_t a3 = ld2(g.A, row0 + gid + 8, g.m, g.lda, ka + 8);
+  const int bm = blockIdx.y * GBM, bn = blockIdx.x * GBN;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  float c[2][4][4];
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int nb = col0 + t * 8 + gid;
-      const uint32_t b0 = ld2(g.B, nb, g.n, g.ldb, ka);
-      const uint32_t b1 = ld2(g.B, nb, g.n, g.ldb, ka + 8);
-      asm volatile(
-          "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-          "{%0,%1,%2,%3};"
-          : "+f"(c[t][0]), "+f"(c[t][1]), "+f"(c[t][2]), "+f"(c[t][3])
-          : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) c[i][j][e] = 0.f;
+  for (int k0 = 0; k0 < g.K; k0 += GBK) {
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {  // 256 chunks of 8 BF16 per operand tile
+      const int chunk = tid + t * 128, r = chunk >> 2, kc = (chunk & 3) * 8;
+      *reinterpret_cast<uint4 *>(&As[r][kc]) = ld16(g.A, bm + r, g.m, g.lda, k0 + kc, g.K);
+      *reinterpret_cast<uint4 *>(&Bs[r][kc]) = ld16(g.B, bn + r, g.n, g.ldb, k0 + kc, g.K);
     }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GBK; kk += 16) {
+      uint32_t a[2][4], b[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + i * 16 + gid;
+        a[i][0] = *reinterpret_cast<const uint32_t *>(&As[r][kk + tig * 2]);
+        a[i][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + tig * 2]);
+        a[i][2] = *reinterpret_cast<const uint32_t *>(&As[r][kk + tig * 2 + 8]);
+        a[i][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + tig * 2 + 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = wn + j * 8 + gid;
+        b[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[r][kk + tig * 2]);
+        b[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[r][kk + tig * 2 + 8]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+              "{%0,%1,%2,%3};"
+              : "+f"(c[i][j][0]), "+f"(c[i][j][1]), "+f"(c[i][j][2]), "+f"(c[i][j][3])
+              : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
+    }
+    __syncthreads();
   }
 #pragma unroll
-  for (int t = 0; t < 2; ++t)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int r = row0 + gid + (e >= 2 ? 8 : 0);
-      const int cc = col0 + t * 8 + tig * 2 + (e & 1);
-      if (r >= g.m || cc >= g.n) continue;
-      float v = c[t][e];
-      if (g.bias) v += g.bias[cc];
-      if (g.relu) v = fmaxf(v, 0.f);
-      if (g.aux && !(__bfloat162float(g.aux[(size_t)r * g.ldaux + cc]) > 0.f)) v = 0.f;
-      if (g.Cf) g.Cf[(size_t)r * g.ldc + cc] = v;
-      else g.Cb[(size_t)r * g.ldc + cc] = __float2bfloat16(v);
-    }
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = bm + wm + i * 16 + gid + (e >= 2 ? 8 : 0);
+        const int cc = bn + wn + j * 8 + tig * 2 + (e & 1);
+        if (r >= g.m || cc >= g.n) continue;
+        float v = c[i][j][e];
+        if (g.bias) v += g.bias[cc];
+        if (g.relu) v = fmaxf(v, 0.f);
+        if (g.aux && !(__bfloat162float(g.aux[(size_t)r * g.ldaux + cc]) > 0.f)) v = 0.f;
+        if (g.Cf) g.Cf[(size_t)r * g.ldc + cc] = v;
+        else g.Cb[(size_t)r * g.ldc + cc] = __float2bfloat16(v);
+      }
 }
 
 static void gemm(const GemmArgs &g, cudaStream_t s) {
-  dim3 grid((g.n + 31) / 32, (g.m + 31) / 32);
+  dim3 grid((g.n + GBN - 1) / GBN, (g.m + GBM - 1) / GBM);
   k_gemm_nt<<<grid, 128, 0, s>>>(g);
 }
 
@@ -489,6 +526,23 @@ int tor_mlp_set_params(tor_mlp *m, const float *host) {
       }
     for (int r = 0; r < realo[l]; ++r) P[m->boff[l] + r] = host[o++];
   }
+  MCK(cudaMemcpy(m->P, P.data(), sizeof(float) * m->nparam, cudaMemcpyHostToDevice));
+  refresh_bf16(m, 0);
+  MCK(cudaDeviceSynchronize());
+  return TOR_OK;
+}
+
+// Start the network at the product of independent marginals: W4 = 0 and
+// b4_j = logit(marg_j), so q(x) = prod_j marg_j^x_j (1 - marg_j)^(1 - x_j) (the
+// plain proposal) until training adds the correlations the hidden layers see.
+int tor_mlp_set_marginals(tor_mlp *m, const double *marg_host) {
+  if (!m || !marg_host) return mfail(TOR_EINVAL, "null pointer");
+  for (int j = 0; j < m->M; ++j)
+    if (!(marg_host[j] > 0.0 && marg_host[j] < 1.0)) return mfail(TOR_EINVAL, "marginals must lie in (0, 1)");
+  std::vector<float> P(m->nparam);
+  MCK(cudaMemcpy(P.data(), m->P, sizeof(float) * m->nparam, cudaMemcpyDeviceToHost));
+  for (size_t e = 0; e < (size_t)m->out_[3] * m->in_[3]; ++e) P[m->woff[3] + e] = 0.f;
+  for (int j = 0; j < m->M; ++j) P[m->boff[3] + j] = (float)log(marg_host[j] / (1.0 - marg_host[j]));
   MCK(cudaMemcpy(m->P, P.data(), sizeof(float) * m->nparam, cudaMemcpyHostToDevice));
   refresh_bf16(m, 0);
   MCK(cudaDeviceSynchronize());

@@ -78,7 +78,7 @@ __device__ __forceinline__ dd SrcPattern::get<TierDD>(int row, int col) const {
 // stack S and eliminate the fixed modes in place; then the depth-first walk.
 template <class Tier, class Src>
 __device__ __forceinline__ void walk_chunk(const Src &src, int k, int r1, unsigned long long c, double *S,
-                                           size_t st, Sums &Sm) {
+                                           size_t st, Sums &Sm, double *Q, size_t sq) {
   using T = typename Tier::T;
   unsigned char pm[64];
   int np = 0;
@@ -103,10 +103,10 @@ __device__ __forceinline__ void walk_chunk(const Src &src, int k, int r1, unsign
     if (Tier::bad(det2) || Tier::bad(a)) Sm.flags |= ST_NOTPD;
     const T y = Tier::rsqrt(det2);
     t = Tier::mul(t, y);
-    if (rp > 0) schur_mem<Tier>(S, S, st, rp, a, b, d, y);
+    if (rp > 0) schur_mem<Tier>(S, st, S, st, rp, a, b, d, y);
   }
   Tier::acc(Sm, t, ((k ^ np) & 1) != 0);
-  dfs_walk<Tier>(S, st, r1, t, np, k, Sm);
+  dfs_walk<Tier>(S, st, r1, t, np, k, Sm, Q, sq);
 }
 
 __host__ __device__ inline void fixed_to_result(const unsigned long long *w8, int k, int tier, int status,

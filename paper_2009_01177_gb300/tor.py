@@ -97,12 +97,15 @@ SIGNATURES = {
     "tor_mlp_num_params": (_I, [_VP]),
     "tor_mlp_get_params": (_I, [_VP, ctypes.POINTER(ctypes.c_float), _I]),
     "tor_mlp_set_params": (_I, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "tor_mlp_set_marginals": (_I, [_VP, ctypes.POINTER(_D)]),
     "tor_mlp_logq": (_I, [_VP, _VP, _I, _VP, _VP]),
     "tor_mlp_logits": (_I, [_VP, _VP, _I, ctypes.POINTER(ctypes.c_float)]),
     "tor_mlp_grad": (_I, [_VP, _VP, _VP, _I, ctypes.POINTER(ctypes.c_float), _VP]),
     "tor_mlp_train_step": (_I, [_VP, _VP, _VP, _I, ctypes.c_float, ctypes.POINTER(ctypes.c_float), _VP]),
     "tor_mlp_sample": (_I, [_VP, _I, _U64, _U64, _VP, _VP, _VP]),
-    "gbs_sample_step": (_I, [_VP, _VP, _I, _I, _D, _VP, _VP, _I, _VP, _VP, _VP, _VP, _U64, _U64, _I, _D, _VP]),
+    "gbs_sample_step": (_I, [_VP, _VP, _I, _I, _D, _VP, _VP, _I, _VP, _VP, _VP, _VP, _U64, _U64, _I, _D, _I,
+                             _VP]),
+    "tor_autotune": (_I, [_VP, _I, _I, ctypes.c_char_p, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "tor_set_timing": (_I, [_VP, _I]),
     "tor_walk_time": (_I, [_VP, ctypes.POINTER(ctypes.c_float)]),
 }
@@ -157,6 +160,16 @@ def pack_patterns(patterns, M: int) -> torch.Tensor:
     for j in range(M):
         out[:, j // 64] |= a[:, j].astype(np.uint64) << np.uint64(j % 64)
     return torch.from_numpy(out.view(np.int64))
+
+
+RESULT_DTYPE = [("hi", "<f8"), ("lo", "<f8"), ("sum_abs", "<f8"), ("err_est", "<f8"), ("tier", "<i4"),
+                ("status", "<i4")]
+
+
+def results_array(out: torch.Tensor, n: int):
+    """The n tor_result records of a uint8 CUDA tensor as a numpy structured array."""
+    import numpy as np
+    return np.frombuffer(out[:n * RESULT_BYTES].cpu().numpy().tobytes(), dtype=np.dtype(RESULT_DTYPE))
 
 
 def results_from_tensor(out: torch.Tensor, n: int):
@@ -285,7 +298,7 @@ class Context:
 
     def sample_step(self, Ofull: torch.Tensor, logdet_sigma: float, patterns: torch.Tensor, logp: torch.Tensor,
                     logq: torch.Tensor, accepted: torch.Tensor, seed: int, step: int, marg_p=None,
-                    proposal=None, prec: str = "fp64", tol: float = 1e-10, stream=None):
+                    proposal=None, prec: str = "fp64", tol: float = 1e-10, k_cap: int = 0, stream=None):
         """gbs_sample_step on device state tensors (patterns int64 (C, W), logp/logq float64, accepted int32)."""
         k2, ld = _mat(Ofull)
         C = patterns.shape[0]
@@ -294,7 +307,14 @@ class Context:
                                         proposal.h if proposal is not None else None, C, patterns.data_ptr(),
                                         logp.data_ptr(), logq.data_ptr(), accepted.data_ptr(),
                                         seed & 0xFFFFFFFFFFFFFFFF, step & 0xFFFFFFFFFFFFFFFF, _PREC[prec], tol,
-                                        _stream(stream)))
+                                        int(k_cap), _stream(stream)))
+
+    def autotune(self, k: int, prec: str = "fp64", cache_path: str | None = None):
+        """Time chunk depths and launch shapes for k clicks; returns (chunk_bits, blocks_per_sm)."""
+        d, b = ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.tor_autotune(self.h, k, _PREC[prec], cache_path.encode() if cache_path else None,
+                                     ctypes.byref(d), ctypes.byref(b)))
+        return d.value, b.value
 
     def set_timing(self, on: bool):
         _check(self.lib.tor_set_timing(self.h, int(bool(on))))
@@ -381,6 +401,12 @@ class MLP:
         if a.size != self.num_params:
             raise ValueError("wrong parameter count")
         _check(self.lib.tor_mlp_set_params(self.h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def set_marginals(self, marg):
+        """Start at the plain proposal (independent clicks with probabilities marg)."""
+        import numpy as np
+        a = np.ascontiguousarray(marg, dtype=np.float64)
+        _check(self.lib.tor_mlp_set_marginals(self.h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
 
     def logq(self, patterns: torch.Tensor, stream=None) -> torch.Tensor:
         B = patterns.shape[0]

@@ -132,3 +132,31 @@ def test_batch_in_cuda_graph_replays_with_new_inputs(ctx, cuda_lib):
         res = cuda_lib.results_from_tensor(out, n)
         direct = ctx.batch([torch.from_numpy(O).cuda() for O in mats])
         assert [(r.hi, r.lo) for r in res] == [(r.hi, r.lo) for r in direct]
+
+
+def test_pattern_batches_accept_larger_k_after_small(ctx):
+    # a first batch of few clicks must not limit a later batch of the same state
+    st = gi.lossy_gbs_state(30, 0.6, 1.2, 0.3, 31)
+    Od = torch.from_numpy(st.O).cuda()
+    small = np.zeros((8, 30), dtype=np.uint8)
+    small[:, :3] = 1
+    big = np.zeros((4, 30), dtype=np.uint8)
+    big[:, :18] = 1
+    ctx.batch_patterns(Od, small)
+    res = ctx.batch_patterns(Od, big)
+    assert all(r.status == 0 for r in res)
+    ref = ctx.single(torch.from_numpy(gi.select(st.O, np.arange(18))).cuda())
+    assert abs(res[0].value - ref.value) <= res[0].err_est + ref.err_est
+
+
+def test_plain_proposal_is_the_initial_network(ctx, cuda_lib):
+    from paper_2009_01177_gb300.tor import pack_patterns
+    M = 12
+    marg = np.linspace(0.1, 0.6, M)
+    net = cuda_lib.MLP(ctx, M, 64, seed=2)
+    net.set_marginals(marg)
+    X = (np.random.default_rng(1).random((64, M)) < 0.4).astype(np.float64)
+    lq = net.logq(pack_patterns(X, M).cuda()).cpu().numpy()
+    ref = (X * np.log(marg) + (1 - X) * np.log1p(-marg)).sum(1)
+    assert np.allclose(lq, ref, atol=1e-5)
+    net.close()

@@ -205,3 +205,38 @@ def test_k32_block_factorisation(ctx):
     assert abs(float(got - prod)) <= r.err_est
     sabs = r1.sum_abs * r2.sum_abs
     assert abs(r.sum_abs - sabs) <= 1e-12 * sabs
+
+
+def test_autotune_picks_and_caches(ctx, tmp_path):
+    cache = str(tmp_path / "tune.jsonl")
+    st, pat, O32 = gi.workload_m100(32)
+    O = gi.select(st.O, pat[:20])
+    before = ctx.single(dev(O))
+    d, bps = ctx.autotune(20, "fp64", cache)
+    assert 0 <= d <= 20 and 1 <= bps <= 4
+    lines = open(cache).read().strip().splitlines()
+    assert len(lines) == 1 and '"k": 20' in lines[0]
+    assert ctx.autotune(20, "fp64", cache) == (d, bps)           # served from the cache
+    assert len(open(cache).read().strip().splitlines()) == 1
+    after = ctx.single(dev(O))
+    assert abs(after.value - before.value) <= after.err_est + before.err_est
+    assert after.sum_abs == pytest.approx(before.sum_abs, rel=1e-12)
+
+
+def test_shard_ranges_gather_to_the_single_result(ctx):
+    from paper_2009_01177_gb300 import shard
+    from paper_2009_01177_gb300.tor import fixed_to_result
+    st, pat, O32 = gi.workload_m100(32)
+    O = gi.select(st.O, pat[:18])
+    Od = dev(O)
+    d, world = 8, 3
+    parts = []
+    for r in range(world):
+        lo, hi = shard.chunk_range(r, world, 1 << d)
+        parts.append(shard.sum_partials(ctx.chunks(Od, d, lo, hi).cpu().numpy().view(np.uint64)))
+    total = shard.sum_partials(np.stack(parts))
+    r_sh = fixed_to_result([int(x) for x in total], 18)
+    ctx.set_chunk_bits(d)
+    r = ctx.single(Od)
+    ctx.set_chunk_bits(-1)
+    assert (r_sh.hi, r_sh.lo, r_sh.sum_abs) == (r.hi, r.lo, r.sum_abs)
