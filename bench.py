@@ -259,6 +259,10 @@ def run_mh(args):
     from paper_2009_01177_gb300 import tor
     ctx = tor.Context(0)
     C = args.n
+    t_start = time.perf_counter()
+
+    def progress(msg):
+        print(f"[mh {time.perf_counter() - t_start:7.1f} s] {msg}", file=sys.stderr, flush=True)
 
     def chains(st, C=C):
         words = (st.M + 63) // 64
@@ -299,10 +303,13 @@ def run_mh(args):
     # M = 60: train on states of the plain exact chain, then race the two proposals
     st = gi.lossy_gbs_state(60, 0.5, 1.0, 0.5, 6)
     marg60 = marginals(st)
-    k_cap = int(round(marg60.sum() + 6 * np.sqrt((marg60 * (1 - marg60)).sum()) + 4))
+    # the cost of one proposal is 2^k subset determinants: both chains target p(S | k <= k_cap)
+    k_cap = int(round(marg60.sum() + 3.5 * np.sqrt((marg60 * (1 - marg60)).sum())))
     ch = chains(st)
     hist = []
+    progress(f"M=60 plain exact chain, k_cap={k_cap}")
     run(ch, 60, 6, record=hist, k_cap=k_cap)
+    progress("training the proposal")
     pool = torch.cat(hist[10:])
     pool = pool[torch.randperm(pool.shape[0], device="cuda")]
     nval = pool.shape[0] // 10
@@ -314,12 +321,13 @@ def run_mh(args):
     res = {}
     steps = max(8, 4 * args.steps)
     for name, prop in (("plain", None), ("learned", net)):
+        progress(f"race: {name}")
         chn = chains(st)
-        run(chn, 3, 7, prop)
+        run(chn, 3, 7, prop, k_cap=k_cap)
         series = []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        acc = run(chn, steps, 7, prop, record=series, t0=100)
+        acc = run(chn, steps, 7, prop, record=series, t0=100, k_cap=k_cap)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         ess = _ess_geyer(np.stack([_click_counts(p) for p in series]).astype(float))
@@ -338,6 +346,7 @@ def run_mh(args):
                                   "plain proposal, trained (3000 Adam steps, batch 4096, best of held-out NLL) on "
                                   "50 x C states of the plain exact chain"}}
     # M = 20: all 2^20 exact probabilities, then TV of the pooled chain states
+    progress("M=20 exact table")
     st20 = gi.lossy_gbs_state(20, 0.5, 1.0, 0.5, 5)
     allx = ((np.arange(1 << 20)[:, None] >> np.arange(20)[None, :]) & 1).astype(np.uint8)
     O20 = torch.from_numpy(st20.O).cuda()
@@ -357,6 +366,7 @@ def run_mh(args):
     tv = {}
     C20 = 16 * C
     for name, prop in (("plain", None), ("learned", net20)):
+        progress(f"M=20 chains: {name}")
         chn = chains(st20, C20)
         run(chn, 20, 9, prop)
         series = []

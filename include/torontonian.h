@@ -62,7 +62,15 @@ enum {
     TOR_ENOMEM = 6      /* workspace allocation failed */
 };
 
-enum { TOR_PREC_AUTO = 0, TOR_PREC_FP64 = 1, TOR_PREC_DD = 2 };
+enum { TOR_PREC_AUTO = 0, TOR_PREC_FP64 = 1, TOR_PREC_DD = 2, TOR_PREC_FX128 = 3 };
+/* TOR_PREC_FX128: the paper's 128-bit fixed point with one scaling factor
+ * (Sec. 5.1-5.2), 104 fraction bits, on the integer pipe.  Every intermediate
+ * must stay below 2^23 in magnitude; the largest are the pivot inverses
+ * 1/det2 <= t_max^2 with t_max = 1/sqrt(det(I - O)), so tor_single requires
+ * t_max <= 2^11 (checked by the bound pass, TOR_EINVAL otherwise); a product
+ * that still leaves the range sets the result's status to TOR_EINVAL.
+ * Available in tor_single, tor_single_async and tor_chunks (the latter two
+ * do not run the range check). */
 enum { TOR_LAYOUT_XXPP = 0, TOR_LAYOUT_XPXP = 1 };
 
 typedef struct tor_ctx tor_ctx;
@@ -72,7 +80,7 @@ typedef struct {
     double hi, lo;      /* Tor = hi + lo */
     double sum_abs;     /* sum_Z t_Z (>= |Tor|) */
     double err_est;     /* a-posteriori bound on |computed - exact| */
-    int tier;           /* TOR_PREC_FP64 or TOR_PREC_DD: arithmetic actually used */
+    int tier;           /* TOR_PREC_FP64, TOR_PREC_DD or TOR_PREC_FX128: arithmetic used */
     int status;         /* TOR_OK or TOR_ENOTPD for this instance */
 } tor_result;
 

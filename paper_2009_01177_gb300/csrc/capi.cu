@@ -60,8 +60,8 @@ struct tor_ctx {
   Buf mh;                // sampler: proposals, their log q, their Torontonians
   unsigned char r1_table[3][65];  // walked modes per chunk, by tier and k
   // autotuned single-instance settings by tier and k (-1: not tuned)
-  signed char tuned_d[3][65];
-  signed char tuned_bps[3][65];
+  signed char tuned_d[4][65];   // by tier (TOR_PREC_FP64 .. TOR_PREC_FX128) and k
+  signed char tuned_bps[4][65];
 };
 
 namespace {
@@ -231,8 +231,8 @@ int tor_single_async(tor_ctx *ctx, const double *O, int k, int ld, int layout, i
   int rc = check_common(ctx, O, k, ld, layout);
   if (rc) return rc;
   if (!out_dev) return fail(TOR_EINVAL, "null result pointer");
-  if (prec != TOR_PREC_FP64 && prec != TOR_PREC_DD)
-    return fail(TOR_EINVAL, "tor_single_async needs TOR_PREC_FP64 or TOR_PREC_DD");
+  if (prec != TOR_PREC_FP64 && prec != TOR_PREC_DD && prec != TOR_PREC_FX128)
+    return fail(TOR_EINVAL, "tor_single_async needs TOR_PREC_FP64, TOR_PREC_DD or TOR_PREC_FX128");
   CK(cudaSetDevice(ctx->device));
   if (k == 0) {
     tor_result one = {1.0, 0.0, 1.0, 0.0, prec, TOR_OK};
@@ -269,9 +269,21 @@ int tor_single(tor_ctx *ctx, const double *O, int k, int ld, int layout, int pre
   int rc = check_common(ctx, O, k, ld, layout);
   if (rc) return rc;
   if (!out) return fail(TOR_EINVAL, "null result pointer");
-  if (prec != TOR_PREC_AUTO && prec != TOR_PREC_FP64 && prec != TOR_PREC_DD)
+  if (prec != TOR_PREC_AUTO && prec != TOR_PREC_FP64 && prec != TOR_PREC_DD && prec != TOR_PREC_FX128)
     return fail(TOR_EINVAL, "bad precision %d", prec);
   int tier = prec;
+  if (prec == TOR_PREC_FX128 && k > 0) {  // the fixed-point range: 1/det2 <= t_max^2 must fit
+    CK(cudaSetDevice(ctx->device));
+    if ((rc = ensure(ctx, ctx->bound, sizeof(tor_bound)))) return rc;
+    if (tor::launch_bounds_single(O, k, ld, layout, 1e-10, (tor_bound *)ctx->bound.p, s))
+      return fail(TOR_ECUDA, "bound pass launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    tor_bound bd;
+    CK(cudaMemcpyAsync(&bd, ctx->bound.p, sizeof(bd), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!(bd.log_tmax <= tor::FX128_MAX_LOG2_TMAX * 0.6931472f))
+      return fail(TOR_EINVAL, "instance outside the 128-bit fixed-point range (log2 t_max = %.2f > %.0f)",
+                  (double)bd.log_tmax / 0.6931472, (double)tor::FX128_MAX_LOG2_TMAX);
+  }
   if (prec == TOR_PREC_AUTO) {
     if (!(tol > 0.0)) return fail(TOR_EINVAL, "TOR_PREC_AUTO needs a tolerance tol > 0");
     tier = TOR_PREC_FP64;
@@ -309,7 +321,8 @@ int tor_chunks(tor_ctx *ctx, const double *O, int k, int ld, int layout, int pre
   int rc = check_common(ctx, O, k, ld, layout);
   if (rc) return rc;
   if (k == 0) return fail(TOR_EINVAL, "tor_chunks needs k >= 1");
-  if (prec != TOR_PREC_FP64 && prec != TOR_PREC_DD) return fail(TOR_EINVAL, "prec must be FP64 or DD");
+  if (prec != TOR_PREC_FP64 && prec != TOR_PREC_DD && prec != TOR_PREC_FX128)
+    return fail(TOR_EINVAL, "prec must be FP64, DD or FX128");
   if (chunk_bits < 0 || chunk_bits > k || chunk_bits > 40) return fail(TOR_EINVAL, "chunk_bits outside [0, min(k, 40)]");
   if (!part_dev) return fail(TOR_EINVAL, "null partials pointer");
   const uint64_t nchunks = 1ull << chunk_bits;
@@ -325,7 +338,7 @@ int tor_chunks(tor_ctx *ctx, const double *O, int k, int ld, int layout, int pre
 
 int tor_fixed_to_result(const uint64_t *limbs8, int k, int tier, tor_result *out) {
   if (!limbs8 || !out) return fail(TOR_EINVAL, "null pointer");
-  if (tier != TOR_PREC_FP64 && tier != TOR_PREC_DD) return fail(TOR_EINVAL, "bad tier");
+  if (tier != TOR_PREC_FP64 && tier != TOR_PREC_DD && tier != TOR_PREC_FX128) return fail(TOR_EINVAL, "bad tier");
   tor::fixed_to_result((const unsigned long long *)limbs8, k, tier, 0, out);
   return TOR_OK;
 }
@@ -436,6 +449,7 @@ static int batch_autoreserve(tor_ctx *ctx, const int *k_dev, int n, cudaStream_t
 static int batch_check(tor_ctx *ctx, int n, int prec, double tol) {
   if (!ctx) return fail(TOR_EINVAL, "null context");
   if (n < 0) return fail(TOR_EINVAL, "n = %d < 0", n);
+  if (prec == TOR_PREC_FX128) return fail(TOR_EINVAL, "batches run FP64, DD or AUTO; FX128 is single-instance");
   if (prec != TOR_PREC_AUTO && prec != TOR_PREC_FP64 && prec != TOR_PREC_DD)
     return fail(TOR_EINVAL, "bad precision %d", prec);
   if (prec == TOR_PREC_AUTO && !(tol > 0.0)) return fail(TOR_EINVAL, "TOR_PREC_AUTO needs tol > 0");
@@ -560,7 +574,7 @@ bool parse_line(const char *line, TuneEntry &e) {
   e.d = atoi(d + 14);
   e.bps = atoi(b + 17);
   e.ms = atof(m + 6);
-  return e.k >= 0 && e.k <= 64 && (e.tier == TOR_PREC_FP64 || e.tier == TOR_PREC_DD) && e.d >= 0 && e.d <= e.k &&
+  return e.k >= 0 && e.k <= 64 && e.tier >= TOR_PREC_FP64 && e.tier <= TOR_PREC_FX128 && e.d >= 0 && e.d <= e.k &&
          e.bps >= 1 && e.bps <= 16;
 }
 
@@ -570,7 +584,8 @@ int tor_autotune(tor_ctx *ctx, int k, int prec, const char *cache_path, int *chu
                  int *blocks_per_sm_out) {
   if (!ctx) return fail(TOR_EINVAL, "null context");
   if (k < 1 || k > 40) return fail(TOR_EINVAL, "autotune k = %d outside [1, 40]", k);
-  if (prec != TOR_PREC_FP64 && prec != TOR_PREC_DD) return fail(TOR_EINVAL, "prec must be FP64 or DD");
+  if (prec != TOR_PREC_FP64 && prec != TOR_PREC_DD && prec != TOR_PREC_FX128)
+    return fail(TOR_EINVAL, "prec must be FP64, DD or FX128");
   CK(cudaSetDevice(ctx->device));
   cudaDeviceProp prop;
   CK(cudaGetDeviceProperties(&prop, ctx->device));
@@ -590,7 +605,7 @@ int tor_autotune(tor_ctx *ctx, int k, int prec, const char *cache_path, int *chu
       if (found) {
         ctx->tuned_d[prec][k] = (signed char)best.d;
         ctx->tuned_bps[prec][k] = (signed char)best.bps;
-        ctx->r1_table[prec][k] = (unsigned char)(k - best.d);
+        if (prec <= TOR_PREC_DD) ctx->r1_table[prec][k] = (unsigned char)(k - best.d);
         if (chunk_bits_out) *chunk_bits_out = best.d;
         if (blocks_per_sm_out) *blocks_per_sm_out = best.bps;
         return TOR_OK;
@@ -652,7 +667,7 @@ int tor_autotune(tor_ctx *ctx, int k, int prec, const char *cache_path, int *chu
   if (rc) return rc;
   ctx->tuned_d[prec][k] = (signed char)best_d;
   ctx->tuned_bps[prec][k] = (signed char)best_bps;
-  ctx->r1_table[prec][k] = (unsigned char)(k - best_d);
+  if (prec <= TOR_PREC_DD) ctx->r1_table[prec][k] = (unsigned char)(k - best_d);
   if (ctx->r1_table_dev)
     CK(cudaMemcpy(ctx->r1_table_dev, ctx->r1_table, sizeof(ctx->r1_table), cudaMemcpyHostToDevice));
   if (cache_path) {

@@ -46,6 +46,7 @@
 #include <cstdint>
 #include "fixacc.cuh"
 #include "dd.cuh"
+#include "fx128.cuh"
 
 namespace tor {
 
@@ -53,7 +54,7 @@ __host__ __device__ constexpr int sz(int r) { return r * (2 * r + 1); }
 __host__ __device__ constexpr int ix(int hi, int lo) { return hi * (hi + 1) / 2 + lo; }
 
 // status bits written by the kernels
-enum : int { ST_NOTPD = 1, ST_RANGE = 2 };
+enum : int { ST_NOTPD = 1, ST_RANGE = 2 };  // ST_RANGE also marks fixed-point overflow
 
 // ----------------------------------------------------------- accumulators
 struct Sums {
@@ -160,27 +161,30 @@ struct TierF64 {
   __device__ static __forceinline__ T ld(const double *P, int e, size_t st) { return P[(size_t)e * st]; }
   __device__ static __forceinline__ void stv(double *P, int e, size_t st, T v) { P[(size_t)e * st] = v; }
   __device__ static __forceinline__ T one() { return 1.0; }
-  __device__ static __forceinline__ T det2(T a, T b, T d) { return fma(a, d, -dmul(b, b)); }
+  __device__ static __forceinline__ T det2(T a, T b, T d, int &) { return fma(a, d, -dmul(b, b)); }
   // not (0 < x < inf): integer test on the bit pattern, no FP64 compare
   __device__ static __forceinline__ bool bad(T x) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(x);
     return (u - 1ull) >= 0x7FEFFFFFFFFFFFFFull;
   }
-  __device__ static __forceinline__ T rsqrt(T x) { return rsqrt_fp64(x); }
-  __device__ static __forceinline__ T mul(T a, T b) { return dmul(a, b); }
+  __device__ static __forceinline__ T rsqrt(T x, int &) { return rsqrt_fp64(x); }
+  __device__ static __forceinline__ T mul(T a, T b, int &) { return dmul(a, b); }
   // pivot coefficients: S_cc^-1 = [[al, -be], [-be, de]] with inv = y^2 = 1/det2
-  __device__ static __forceinline__ void coef(T a, T b, T d, T y, T &al, T &be, T &de) {
+  __device__ static __forceinline__ void coef(T a, T b, T d, T y, T &al, T &be, T &de, int &) {
     const T inv = dmul(y, y);
     al = dmul(d, inv); be = dmul(b, inv); de = dmul(a, inv);
   }
   // v = S_cc^-1 u
-  __device__ static __forceinline__ void vrow(T al, T be, T de, T ux, T up, T &vx, T &vp) {
+  __device__ static __forceinline__ void vrow(T al, T be, T de, T ux, T up, T &vx, T &vp, int &) {
     vx = fma(al, ux, -dmul(be, up));
     vp = fma(de, up, -dmul(be, ux));
   }
-  __device__ static __forceinline__ T upd(T s, T vx, T ux, T vp, T up) {
+  __device__ static __forceinline__ T upd(T s, T vx, T ux, T vp, T up, int &) {
     return fma(-vp, up, fma(-vx, ux, s));
   }
+  // entries of B = I - O: from the prepped (rounded 1 - o, exact low part) pair, or from o
+  __device__ static __forceinline__ T from_hilo(double h, double) { return h; }
+  __device__ static __forceinline__ T from_o(double o, bool diag) { return diag ? 1.0 - o : -o; }
   __device__ static __forceinline__ void acc(Sums &S, T t, bool neg) {
     fx_add_signed(S.tor, t, neg, S.flags);
     fx_add_signed(S.sabs, t, false, S.flags);
@@ -203,26 +207,137 @@ struct TierDD {
     P[(size_t)(2 * e + 1) * st] = v.lo;
   }
   __device__ static __forceinline__ T one() { return {1.0, 0.0}; }
-  __device__ static __forceinline__ T det2(T a, T b, T d) { return dd_det2(a, b, d); }
+  __device__ static __forceinline__ T det2(T a, T b, T d, int &) { return dd_det2(a, b, d); }
   __device__ static __forceinline__ bool bad(T x) { return TierF64::bad(x.hi); }
-  __device__ static __forceinline__ T rsqrt(T x) { return dd_rsqrt(x, TierF64::rsqrt(x.hi)); }
-  __device__ static __forceinline__ T mul(T a, T b) { return dd_mul(a, b); }
-  __device__ static __forceinline__ void coef(T a, T b, T d, T y, T &al, T &be, T &de) {
+  __device__ static __forceinline__ T rsqrt(T x, int &) { return dd_rsqrt(x, rsqrt_fp64(x.hi)); }
+  __device__ static __forceinline__ T mul(T a, T b, int &) { return dd_mul(a, b); }
+  __device__ static __forceinline__ void coef(T a, T b, T d, T y, T &al, T &be, T &de, int &) {
     const T inv = dd_mul(y, y);
     al = dd_mul(d, inv); be = dd_mul(b, inv); de = dd_mul(a, inv);
   }
-  __device__ static __forceinline__ void vrow(T al, T be, T de, T ux, T up, T &vx, T &vp) {
+  __device__ static __forceinline__ void vrow(T al, T be, T de, T ux, T up, T &vx, T &vp, int &) {
     vx = dd_add(dd_mul(al, ux), dd_neg(dd_mul(be, up)));
     vp = dd_add(dd_mul(de, up), dd_neg(dd_mul(be, ux)));
   }
-  __device__ static __forceinline__ T upd(T s, T vx, T ux, T vp, T up) {
+  __device__ static __forceinline__ T upd(T s, T vx, T ux, T vp, T up, int &) {
     return dd_rank2_update(s, vx, ux, vp, up);
   }
+  __device__ static __forceinline__ T from_hilo(double h, double l) { return {h, l}; }
+  __device__ static __forceinline__ T from_o(double o, bool diag) { return diag ? two_sum(1.0, -o) : dd{-o, 0.0}; }
   __device__ static __forceinline__ void acc(Sums &S, T t, bool neg) {
     fx_add_signed(S.tor, t.hi, neg, S.flags);
     fx_add_signed(S.tor, t.lo, neg, S.flags);
     fx_add_signed(S.sabs, t.hi, false, S.flags);
     fx_add_signed(S.sabs, t.lo, false, S.flags);
+  }
+};
+
+// ------------------------------------------------- 128-bit fixed-point tier
+// Values are 128-bit two's-complement integers with F fraction bits (one
+// scale for the whole instance, Sec. 5.1-5.2), stored as two 64-bit words in
+// the same 16-byte entries as the double-double tier.  The caller picks F so
+// that every intermediate stays below 2^(126-F).  Products are the only
+// rounding (toward zero, Sec. 5.1) and set ST_RANGE if they overflow.
+template <int F>
+struct TierFx {
+  using T = fx;
+  static constexpr int W = 2;
+  static constexpr int RREG = 2;
+  static constexpr int RUNROLL = 0;
+  static constexpr int RSMEM = TOR_DD_RSMEM;
+  static constexpr int FRAC = F;
+  static_assert(F >= 64 && F <= 124, "fraction bits");
+
+  __device__ static __forceinline__ T ld(const double *P, int e, size_t st) {
+    return {(unsigned long long)__double_as_longlong(P[(size_t)(2 * e) * st]),
+            __double_as_longlong(P[(size_t)(2 * e + 1) * st])};
+  }
+  __device__ static __forceinline__ void stv(double *P, int e, size_t st, T v) {
+    P[(size_t)(2 * e) * st] = __longlong_as_double((long long)v.lo);
+    P[(size_t)(2 * e + 1) * st] = __longlong_as_double(v.hi);
+  }
+  __device__ static __forceinline__ T one() { return {0ull, 1ll << (F - 64)}; }
+  // exact for 2^(53-F) <= |x| < 2^(126-F); smaller magnitudes lose their low bits
+  __device__ static __forceinline__ T from_double(double x, int &fl) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7FF);
+    if (e == 0) return {0ull, 0ll};
+    const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    const int sh = e - 1075 + F;  // value = m 2^sh in units of 2^-F
+    T r;
+    if (sh >= 64) {
+      if (sh + 53 > 127) fl |= ST_RANGE;
+      r = {0ull, (long long)(m << (sh - 64))};
+    } else if (sh > 0) {
+      r = {m << sh, (long long)(m >> (64 - sh))};
+    } else if (sh > -64) {
+      r = {m >> (-sh), 0ll};
+    } else {
+      r = {0ull, 0ll};
+    }
+    return (bits >> 63) ? fx_neg(r) : r;
+  }
+  __device__ static __forceinline__ double to_double(const T &x) {
+    const bool neg = x.hi < 0;
+    const T m = neg ? fx_neg(x) : x;
+    const double d = ((double)(unsigned long long)m.hi * 18446744073709551616.0 + (double)m.lo) *
+                     __longlong_as_double((long long)(1023 - F) << 52);  // * 2^-F
+    return neg ? -d : d;
+  }
+  __device__ static __forceinline__ T from_hilo(double h, double l) {
+    int fl = 0;
+    return fx_add(from_double(h, fl), from_double(l, fl));
+  }
+  __device__ static __forceinline__ T from_o(double o, bool diag) {
+    int fl = 0;
+    const T v = from_double(o, fl);
+    return diag ? fx_sub(one(), v) : fx_neg(v);
+  }
+  __device__ static __forceinline__ T mul(T a, T b, int &fl) {
+    int o = 0;
+    const T r = fx_mul(a, b, F, o);
+    if (o) fl |= ST_RANGE;
+    return r;
+  }
+  __device__ static __forceinline__ T det2(T a, T b, T d, int &fl) { return fx_sub(mul(a, d, fl), mul(b, b, fl)); }
+  __device__ static __forceinline__ bool bad(T x) { return x.hi < 0 || (x.hi == 0 && x.lo == 0ull); }
+  // 1/sqrt(x): the FP64 pipe (idle in this tier) gives a ~53-bit seed, two fixed-point
+  // Newton steps y <- y (3 - x y^2) / 2 take it to the full fraction width
+  __device__ static __forceinline__ T rsqrt(T x, int &fl) {
+    const double xd = to_double(x);
+    T y = from_double(xd > 0.0 ? rsqrt_fp64(xd) : 0.0, fl);
+    const T three = {0ull, 3ll << (F - 64)};
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const T e = fx_sub(three, mul(x, mul(y, y, fl), fl));
+      const T p = mul(y, e, fl);
+      y = {(p.lo >> 1) | ((unsigned long long)p.hi << 63), p.hi >> 1};  // / 2 (arithmetic shift)
+    }
+    return y;
+  }
+  __device__ static __forceinline__ void coef(T a, T b, T d, T y, T &al, T &be, T &de, int &fl) {
+    const T inv = mul(y, y, fl);
+    al = mul(d, inv, fl); be = mul(b, inv, fl); de = mul(a, inv, fl);
+  }
+  __device__ static __forceinline__ void vrow(T al, T be, T de, T ux, T up, T &vx, T &vp, int &fl) {
+    vx = fx_sub(mul(al, ux, fl), mul(be, up, fl));
+    vp = fx_sub(mul(de, up, fl), mul(be, ux, fl));
+  }
+  __device__ static __forceinline__ T upd(T s, T vx, T ux, T vp, T up, int &fl) {
+    return fx_sub(fx_sub(s, mul(vx, ux, fl)), mul(vp, up, fl));
+  }
+  // t (F fraction bits, positive) into the 128-fraction-bit accumulators, exactly
+  __device__ static __forceinline__ void acc(Sums &S, T t, bool neg) {
+    if (t.hi < 0) { S.flags |= ST_RANGE; return; }
+    const int sh = 128 - F;  // 4..64
+    Fx256 X;
+    const unsigned long long hi = (unsigned long long)t.hi;
+    X.w[0] = (sh == 64) ? 0ull : (t.lo << sh);
+    X.w[1] = (sh == 64) ? t.lo : ((hi << sh) | (t.lo >> (64 - sh)));
+    X.w[2] = (sh == 64) ? hi : (hi >> (64 - sh));
+    X.w[3] = 0ull;
+    if (neg) fx_sub(S.tor, X); else fx_add(S.tor, X);
+    fx_add(S.sabs, X);
   }
 };
 
@@ -236,8 +351,9 @@ __device__ __forceinline__ void reg_child(const Get &get, typename Tier::T a, ty
                                           typename Tier::T d, typename Tier::T y,
                                           typename Tier::T tc, int parc, int k, Sums &S) {
   using T = typename Tier::T;
+  int &FL = S.flags;
   T al, be, de;
-  Tier::coef(a, b, d, y, al, be, de);
+  Tier::coef(a, b, d, y, al, be, de, FL);
   T ux[2 * RP], up[2 * RP];
 #pragma unroll
   for (int i = 0; i < 2 * RP; ++i) {
@@ -248,9 +364,9 @@ __device__ __forceinline__ void reg_child(const Get &get, typename Tier::T a, ty
 #pragma unroll
   for (int i = 0; i < 2 * RP; ++i) {
     T vx, vp;
-    Tier::vrow(al, be, de, ux[i], up[i], vx, vp);
+    Tier::vrow(al, be, de, ux[i], up[i], vx, vp, FL);
 #pragma unroll
-    for (int j = 0; j <= i; ++j) C[ix(i, j)] = Tier::upd(get(ix(i, j)), vx, ux[j], vp, up[j]);
+    for (int j = 0; j <= i; ++j) C[ix(i, j)] = Tier::upd(get(ix(i, j)), vx, ux[j], vp, up[j], FL);
   }
   RegNode<Tier, RP>::visit(C, tc, parc, k, S);
 }
@@ -259,11 +375,12 @@ template <class Tier, int R, int RP>
 struct RegChildren {
   using T = typename Tier::T;
   __device__ static __forceinline__ void run(const T (&M)[sz(R)], T t, int par, int k, Sums &S) {
+    int &FL = S.flags;
     const T a = M[ix(2 * RP + 1, 2 * RP + 1)], b = M[ix(2 * RP + 1, 2 * RP)], d = M[ix(2 * RP, 2 * RP)];
-    const T det2 = Tier::det2(a, b, d);
+    const T det2 = Tier::det2(a, b, d, FL);
     if (Tier::bad(det2) || Tier::bad(a)) S.flags |= ST_NOTPD;  // 2x2 block PD iff a > 0 and det > 0
-    const T y = Tier::rsqrt(det2);
-    const T tc = Tier::mul(t, y);
+    const T y = Tier::rsqrt(det2, FL);
+    const T tc = Tier::mul(t, y, FL);
     Tier::acc(S, tc, ((k ^ (par + 1)) & 1) != 0);
     if constexpr (RP > 0) {
       auto get = [&](int e) { return M[e]; };
@@ -305,21 +422,21 @@ __device__ __forceinline__ void mem_to_reg_child(int rp, const double *P, size_t
 template <class Tier>
 __device__ __noinline__ void schur_mem_loop(const double *P, size_t sp, double *C, size_t sc, int rp,
                                             typename Tier::T a, typename Tier::T b,
-                                            typename Tier::T d, typename Tier::T y) {
+                                            typename Tier::T d, typename Tier::T y, int &FL) {
   using T = typename Tier::T;
   T al, be, de;
-  Tier::coef(a, b, d, y, al, be, de);
+  Tier::coef(a, b, d, y, al, be, de, FL);
   const int n2 = 2 * rp;
   const int cx = ix(2 * rp + 1, 0), cp = ix(2 * rp, 0);
   for (int i = 0; i < n2; ++i) {
     const T uxi = Tier::ld(P, cx + i, sp), upi = Tier::ld(P, cp + i, sp);
     T vx, vp;
-    Tier::vrow(al, be, de, uxi, upi, vx, vp);
+    Tier::vrow(al, be, de, uxi, upi, vx, vp, FL);
     const int row = ix(i, 0);
 #pragma unroll 4
     for (int j = 0; j <= i; ++j) {
       const T s = Tier::ld(P, row + j, sp);
-      Tier::stv(C, row + j, sc, Tier::upd(s, vx, Tier::ld(P, cx + j, sp), vp, Tier::ld(P, cp + j, sp)));
+      Tier::stv(C, row + j, sc, Tier::upd(s, vx, Tier::ld(P, cx + j, sp), vp, Tier::ld(P, cp + j, sp), FL));
     }
   }
 }
@@ -332,10 +449,10 @@ __device__ __noinline__ void schur_mem_loop(const double *P, size_t sp, double *
 template <class Tier, int RP>
 __device__ __forceinline__ void schur_mem_fixed(const double *__restrict__ P, size_t sp, double *__restrict__ C,
                                                 size_t sc, typename Tier::T a, typename Tier::T b,
-                                                typename Tier::T d, typename Tier::T y) {
+                                                typename Tier::T d, typename Tier::T y, int &FL) {
   using T = typename Tier::T;
   T al, be, de;
-  Tier::coef(a, b, d, y, al, be, de);
+  Tier::coef(a, b, d, y, al, be, de, FL);
   T ux[2 * RP], up[2 * RP];
 #pragma unroll
   for (int i = 0; i < 2 * RP; ++i) {
@@ -345,22 +462,22 @@ __device__ __forceinline__ void schur_mem_fixed(const double *__restrict__ P, si
 #pragma unroll
   for (int i = 0; i < 2 * RP; ++i) {
     T vx, vp;
-    Tier::vrow(al, be, de, ux[i], up[i], vx, vp);
+    Tier::vrow(al, be, de, ux[i], up[i], vx, vp, FL);
 #pragma unroll
     for (int j = 0; j <= i; ++j)
-      Tier::stv(C, ix(i, j), sc, Tier::upd(Tier::ld(P, ix(i, j), sp), vx, ux[j], vp, up[j]));
+      Tier::stv(C, ix(i, j), sc, Tier::upd(Tier::ld(P, ix(i, j), sp), vx, ux[j], vp, up[j], FL));
   }
 }
 
 template <class Tier, int RP>
 __device__ __forceinline__ bool schur_try(int rp, const double *P, size_t sp, double *C, size_t sc,
                                           typename Tier::T a, typename Tier::T b,
-                                          typename Tier::T d, typename Tier::T y) {
+                                          typename Tier::T d, typename Tier::T y, int &FL) {
   if constexpr (RP > Tier::RUNROLL) {
     return false;
   } else {
-    if (rp == RP) { schur_mem_fixed<Tier, RP>(P, sp, C, sc, a, b, d, y); return true; }
-    return schur_try<Tier, RP + 1>(rp, P, sp, C, sc, a, b, d, y);
+    if (rp == RP) { schur_mem_fixed<Tier, RP>(P, sp, C, sc, a, b, d, y, FL); return true; }
+    return schur_try<Tier, RP + 1>(rp, P, sp, C, sc, a, b, d, y, FL);
   }
 }
 
@@ -369,9 +486,9 @@ __device__ __forceinline__ bool schur_try(int rp, const double *P, size_t sp, do
 template <class Tier>
 __device__ __noinline__ void schur_mem(const double *P, size_t sp, double *C, size_t sc, int rp,
                                        typename Tier::T a, typename Tier::T b,
-                                       typename Tier::T d, typename Tier::T y) {
-  if (!schur_try<Tier, Tier::RREG + 1>(rp, P, sp, C, sc, a, b, d, y))
-    schur_mem_loop<Tier>(P, sp, C, sc, rp, a, b, d, y);
+                                       typename Tier::T d, typename Tier::T y, int &FL) {
+  if (!schur_try<Tier, Tier::RREG + 1>(rp, P, sp, C, sc, a, b, d, y, FL))
+    schur_mem_loop<Tier>(P, sp, C, sc, rp, a, b, d, y, FL);
 }
 
 // per-thread stack extent (in entries) of a walk over r modes
@@ -394,6 +511,7 @@ __device__ void dfs_walk(double *S, size_t st, int r, typename Tier::T t, int pa
   Frame stk[33];
   int sp = 0;
   int off = 0, rp = 0;
+  int &FL = Sm.flags;
   bool insm = false;  // the current node lives in the shared-memory slot
   while (true) {
     if (rp < r) {
@@ -403,10 +521,10 @@ __device__ void dfs_walk(double *S, size_t st, int r, typename Tier::T t, int pa
       const T a = Tier::ld(P, ix(2 * cur + 1, 2 * cur + 1), ps);
       const T b = Tier::ld(P, ix(2 * cur + 1, 2 * cur), ps);
       const T d = Tier::ld(P, ix(2 * cur, 2 * cur), ps);
-      const T det2 = Tier::det2(a, b, d);
+      const T det2 = Tier::det2(a, b, d, FL);
       if (Tier::bad(det2) || Tier::bad(a)) Sm.flags |= ST_NOTPD;
-      const T y = Tier::rsqrt(det2);
-      const T tc = Tier::mul(t, y);
+      const T y = Tier::rsqrt(det2, FL);
+      const T tc = Tier::mul(t, y, FL);
       Tier::acc(Sm, tc, ((k ^ (par + 1)) & 1) != 0);
       if (cur == 0) continue;
       if (cur <= Tier::RREG) {
@@ -414,18 +532,18 @@ __device__ void dfs_walk(double *S, size_t st, int r, typename Tier::T t, int pa
         continue;
       }
       if (Q && cur <= Tier::RSMEM) {  // into the shared-memory slot (in place when already there)
-        schur_mem<Tier>(P, ps, Q, sq, cur, a, b, d, y);
+        schur_mem<Tier>(P, ps, Q, sq, cur, a, b, d, y, FL);
         if (!insm && cur != r - 1) stk[sp++] = Frame{off, r, rp, par, t};
         insm = true; r = cur; rp = 0; t = tc; par = par + 1;
         continue;
       }
       if (cur == r - 1) {  // last child: in place, the node is finished afterwards
-        schur_mem<Tier>(P, st, const_cast<double *>(P), st, cur, a, b, d, y);
+        schur_mem<Tier>(P, st, const_cast<double *>(P), st, cur, a, b, d, y, FL);
         r = cur; rp = 0; t = tc; par = par + 1;
         continue;
       }
       const int coff = off + sz(r);
-      schur_mem<Tier>(P, st, S + (size_t)(coff * Tier::W) * st, st, cur, a, b, d, y);
+      schur_mem<Tier>(P, st, S + (size_t)(coff * Tier::W) * st, st, cur, a, b, d, y, FL);
       stk[sp++] = Frame{off, r, rp, par, t};
       off = coff; r = cur; rp = 0; t = tc; par = par + 1;
     } else {

@@ -10,9 +10,14 @@ namespace tor {
 // one product per level of its subset (at most k levels), plus the backward
 // error of the Schur updates; gamma = 4k covers those with margin.
 __host__ __device__ inline double err_gamma(int k) { return 4.0 * (k > 1 ? k : 1); }
+// fixed point: absolute rounding 2^-104 per product, relative 2^-100 for the
+// values >= 1/16 the walk carries (Schur entries, pivots, terms)
 __host__ __device__ inline double unit_roundoff(int tier) {
-  return tier == TOR_PREC_DD ? 0x1p-104 : 0x1p-53;
+  return tier == TOR_PREC_DD ? 0x1p-104 : (tier == TOR_PREC_FX128 ? 0x1p-100 : 0x1p-53);
 }
+constexpr int FX128_FRAC = 104;
+// largest log2 t_max for which every intermediate fits: 2 log2 t_max < 127 - F - 1
+constexpr float FX128_MAX_LOG2_TMAX = 11.0f;
 
 // device arrays of a batch plan (sized for n_max instances by tor_batch_reserve)
 struct BatchPlan {

@@ -137,6 +137,11 @@ void launch_dfs(int tier, int grid, int block, const double *B, const double *Bl
     const size_t sm = walk_smem_bytes<TierDD>(block);
     cudaFuncSetAttribute(k_dfs<TierDD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_dfs<TierDD><<<grid, block, sm, s>>>(B, Blo, k, r1, c0, c1, scratch, block_part, chunk_part, status);
+  } else if (tier == TOR_PREC_FX128) {
+    using TF = TierFx<FX128_FRAC>;
+    const size_t sm = walk_smem_bytes<TF>(block);
+    cudaFuncSetAttribute(k_dfs<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_dfs<TF><<<grid, block, sm, s>>>(B, Blo, k, r1, c0, c1, scratch, block_part, chunk_part, status);
   } else {
     const size_t sm = walk_smem_bytes<TierF64>(block);
     cudaFuncSetAttribute(k_dfs<TierF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -151,6 +156,11 @@ int dfs_max_blocks_per_sm(int tier, int block) {
     const size_t sm = walk_smem_bytes<TierDD>(block);
     cudaFuncSetAttribute(k_dfs<TierDD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dfs<TierDD>, block, sm);
+  } else if (tier == TOR_PREC_FX128) {
+    using TF = TierFx<FX128_FRAC>;
+    const size_t sm = walk_smem_bytes<TF>(block);
+    cudaFuncSetAttribute(k_dfs<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dfs<TF>, block, sm);
   } else {
     const size_t sm = walk_smem_bytes<TierF64>(block);
     cudaFuncSetAttribute(k_dfs<TierF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -169,8 +179,9 @@ void launch_dfma_peak(double *sink, int grid, int block, int iters, cudaStream_t
 }
 
 int scratch_entries(int tier, int k, int r1) {
-  const int rreg = (tier == TOR_PREC_DD) ? TierDD::RREG : TierF64::RREG;
-  const int w = (tier == TOR_PREC_DD) ? 2 : 1;
+  const int rreg = (tier == TOR_PREC_DD) ? TierDD::RREG
+                   : (tier == TOR_PREC_FX128) ? TierFx<FX128_FRAC>::RREG : TierF64::RREG;
+  const int w = (tier == TOR_PREC_FP64) ? 1 : 2;
   const int a = sz(k), b = stack_entries(r1, rreg);
   return w * (a > b ? a : b);
 }

@@ -7,24 +7,18 @@
 namespace tor {
 
 // B = I - O entries as the tier's type, from the prepped mode-interleaved matrix
+// (diagonal rounded in B, its exact remainder in Blo)
 struct SrcPrepped {
   const double *__restrict__ B;
   const double *__restrict__ Blo;
   int n2k;
   template <class Tier>
-  __device__ __forceinline__ typename Tier::T get(int row, int col) const;
+  __device__ __forceinline__ typename Tier::T get(int row, int col) const {
+    return Tier::from_hilo(B[(size_t)row * n2k + col], (row == col) ? Blo[row] : 0.0);
+  }
 };
-template <>
-__device__ __forceinline__ double SrcPrepped::get<TierF64>(int row, int col) const {
-  return B[(size_t)row * n2k + col];
-}
-template <>
-__device__ __forceinline__ dd SrcPrepped::get<TierDD>(int row, int col) const {
-  return {B[(size_t)row * n2k + col], (row == col) ? Blo[row] : 0.0};
-}
 
-// B = I - O entries straight from the caller's O (xxpp or xpxp, leading dim ld):
-// 1 - o on the diagonal is rounded once (FP64) or kept exact as a two-sum (dd)
+// B = I - O entries straight from the caller's O (xxpp or xpxp, leading dim ld)
 struct SrcDirect {
   const double *__restrict__ O;
   int k, ld, layout;
@@ -34,18 +28,10 @@ struct SrcDirect {
     return O[(size_t)ri * ld + rj];
   }
   template <class Tier>
-  __device__ __forceinline__ typename Tier::T get(int row, int col) const;
+  __device__ __forceinline__ typename Tier::T get(int row, int col) const {
+    return Tier::from_o(o(row, col), row == col);
+  }
 };
-template <>
-__device__ __forceinline__ double SrcDirect::get<TierF64>(int row, int col) const {
-  const double v = o(row, col);
-  return row == col ? 1.0 - v : -v;
-}
-template <>
-__device__ __forceinline__ dd SrcDirect::get<TierDD>(int row, int col) const {
-  const double v = o(row, col);
-  return row == col ? two_sum(1.0, -v) : dd{-v, 0.0};
-}
 
 // B = I - O_S entries for a click pattern S of the full M-mode matrix O (xxpp,
 // leading dim ld): local mode m is the m-th clicked mode gm[m], whose x and p
@@ -60,18 +46,10 @@ struct SrcPattern {
     return O[(size_t)gr * ld + gc];
   }
   template <class Tier>
-  __device__ __forceinline__ typename Tier::T get(int row, int col) const;
+  __device__ __forceinline__ typename Tier::T get(int row, int col) const {
+    return Tier::from_o(o(row, col), row == col);
+  }
 };
-template <>
-__device__ __forceinline__ double SrcPattern::get<TierF64>(int row, int col) const {
-  const double v = o(row, col);
-  return row == col ? 1.0 - v : -v;
-}
-template <>
-__device__ __forceinline__ dd SrcPattern::get<TierDD>(int row, int col) const {
-  const double v = o(row, col);
-  return row == col ? two_sum(1.0, -v) : dd{-v, 0.0};
-}
 
 // One chunk: the subsets whose high modes r1..k-1 are fixed by the bits of c.
 // Root: gather B over the fixed modes then the low modes into the thread's
@@ -99,11 +77,11 @@ __device__ __forceinline__ void walk_chunk(const Src &src, int k, int r1, unsign
     const T a = Tier::ld(S, ix(2 * rp + 1, 2 * rp + 1), st);
     const T b = Tier::ld(S, ix(2 * rp + 1, 2 * rp), st);
     const T d = Tier::ld(S, ix(2 * rp, 2 * rp), st);
-    const T det2 = Tier::det2(a, b, d);
+    const T det2 = Tier::det2(a, b, d, Sm.flags);
     if (Tier::bad(det2) || Tier::bad(a)) Sm.flags |= ST_NOTPD;
-    const T y = Tier::rsqrt(det2);
-    t = Tier::mul(t, y);
-    if (rp > 0) schur_mem<Tier>(S, st, S, st, rp, a, b, d, y);
+    const T y = Tier::rsqrt(det2, Sm.flags);
+    t = Tier::mul(t, y, Sm.flags);
+    if (rp > 0) schur_mem<Tier>(S, st, S, st, rp, a, b, d, y, Sm.flags);
   }
   Tier::acc(Sm, t, ((k ^ np) & 1) != 0);
   dfs_walk<Tier>(S, st, r1, t, np, k, Sm, Q, sq);

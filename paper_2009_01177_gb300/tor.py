@@ -18,9 +18,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtorontonian.so")
 
 TOR_OK, TOR_EINVAL, TOR_ENOTPD, TOR_ECUDA, TOR_ETIMEOUT, TOR_EPREC, TOR_ENOMEM = range(7)
-PREC_AUTO, PREC_FP64, PREC_DD = 0, 1, 2
+PREC_AUTO, PREC_FP64, PREC_DD, PREC_FX128 = 0, 1, 2, 3
 LAYOUT_XXPP, LAYOUT_XPXP = 0, 1
-_PREC = {"auto": PREC_AUTO, "fp64": PREC_FP64, "dd": PREC_DD}
+_PREC = {"auto": PREC_AUTO, "fp64": PREC_FP64, "dd": PREC_DD, "fx128": PREC_FX128}
 _LAYOUT = {"xxpp": LAYOUT_XXPP, "xpxp": LAYOUT_XPXP}
 
 

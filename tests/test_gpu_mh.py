@@ -132,3 +132,21 @@ def test_learned_proposal_beats_plain(ctx, cuda_lib):
     # and the chains start (and stay) closer to p while the plain chains are still burning in
     assert tv_learn[0] < tv_plain[0] and tv_learn[1] < tv_plain[1], results
     net.close()
+
+
+def test_click_cap_targets_the_conditional_distribution(ctx):
+    st = gi.lossy_gbs_state(6, 0.5, 1.1, 0.7, 64)
+    M, k_cap = st.M, 2
+    p = exact_probs(st)
+    clicks = np.array([bin(c).count("1") for c in range(1 << M)])
+    p_cond = np.where(clicks <= k_cap, p, 0.0)
+    p_cond /= p_cond.sum()
+    ch = Chains(st, 8192)
+    for step in range(40):
+        ctx.sample_step(ch.O, ch.logdet, ch.pat, ch.logp, ch.logq, ch.acc, 91, step,
+                        marg_p=ch.marg, prec="auto", tol=1e-9, k_cap=k_cap)
+        codes = ch.pat[:, 0].cpu().numpy()
+        # a chain holds its initial empty pattern until a proposal within the cap is accepted
+        assert clicks[codes].max() <= k_cap
+    freq = np.bincount(codes, minlength=1 << M) / ch.C
+    assert 0.5 * np.abs(freq - p_cond).sum() < 0.05

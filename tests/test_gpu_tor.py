@@ -240,3 +240,59 @@ def test_shard_ranges_gather_to_the_single_result(ctx):
     r = ctx.single(Od)
     ctx.set_chunk_bits(-1)
     assert (r_sh.hi, r_sh.lo, r_sh.sum_abs) == (r.hi, r.lo, r.sum_abs)
+
+
+# ------------------------------------------------------- 128-bit fixed point
+@pytest.mark.parametrize("k", [1, 4, 9, 13])
+def test_fx128_thermal_closed_form(ctx, k):
+    r = ctx.single(dev(gi.thermal_O(k, 0.25)), prec="fx128")
+    exact = Fraction(1, 3) ** k
+    got = Fraction(r.hi) + Fraction(r.lo)
+    assert r.tier == 3
+    assert abs(float(got - exact)) <= r.err_est
+    assert r.err_est <= 1e-16 * float(exact)     # kappa = (7/3)^k / (1/3)^k = 7^k at most 1e11 here
+
+
+@pytest.mark.parametrize("k", [10, 14, 16, 20])
+def test_fx128_against_oracle(ctx, k):
+    st, pat, O32 = gi.workload_m100(32)
+    O = gi.select(st.O, pat[:k])
+    ref = oracle.tor(O)
+    r = ctx.single(dev(O), prec="fx128")
+    e = err_vs(r, ref)
+    assert r.status == 0 and e <= r.err_est
+    # absolute truncation 2^-104 per product: measured errors sit near 2^-110 sum_Z t_Z
+    assert e <= 2.0 ** -100 * r.sum_abs
+    check(r, ref, "dd")                           # the 1e-20 target wherever the bound allows it
+
+
+def test_fx128_agrees_with_double_double_at_k32(ctx):
+    st, pat, O = gi.workload_m100(32)         # t_max = 2^8.3: 1/det2 up to 2^16.6, inside the range
+    Od = dev(O)
+    fx = ctx.single(Od, prec="fx128")
+    dd = ctx.single(Od, prec="dd")
+    assert fx.status == 0 and fx.tier == 3
+    diff = abs((Fraction(fx.hi) + Fraction(fx.lo)) - (Fraction(dd.hi) + Fraction(dd.lo)))
+    assert float(diff) <= fx.err_est + dd.err_est
+    assert float(diff) <= 2.0 ** -100 * fx.sum_abs  # two independent ~104-bit evaluations agree
+
+
+def test_fx128_chunks_add_to_single(ctx):
+    st, pat, O32 = gi.workload_m100(32)
+    O = gi.select(st.O, pat[:16])
+    Od = dev(O)
+    from paper_2009_01177_gb300 import shard
+    from paper_2009_01177_gb300.tor import fixed_to_result
+    tot = shard.sum_partials(ctx.chunks(Od, 6, 0, 64, prec="fx128").cpu().numpy().view(np.uint64))
+    r_sh = fixed_to_result([int(x) for x in tot], 16, "fx128")
+    ctx.set_chunk_bits(6)
+    r = ctx.single(Od, prec="fx128")
+    ctx.set_chunk_bits(-1)
+    assert (r_sh.hi, r_sh.lo) == (r.hi, r.lo)
+
+
+def test_fx128_rejects_out_of_range(ctx, cuda_lib):
+    O = 0.99 * np.eye(40)      # t_max = 0.01^-20: beyond the fixed-point range
+    with pytest.raises(cuda_lib.TorError) as ei:
+        ctx.single(dev(O), prec="fx128")
+    assert ei.value.code == cuda_lib.TOR_EINVAL
