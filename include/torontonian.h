@@ -118,12 +118,13 @@ int tor_set_chunk_bits(tor_ctx *ctx, int chunk_bits);
 /*
  * tor_single: Tor of one 2k x 2k matrix (Eq. 2).
  *   O     dev  2k x 2k FP64, leading dimension ld, in `layout` order.
- *   prec  TOR_PREC_FP64, TOR_PREC_DD, or TOR_PREC_AUTO: the FP32 bound pass
- *         of tor_bounds picks the starting tier for relative tolerance
- *         `tol`; if the result's a-posteriori bound err_est exceeds
- *         tol * |Tor| in FP64 it is recomputed in double-double, and if it
- *         still does the call returns TOR_EPREC with the result filled in.
- *         `tol` is ignored for the explicit tiers.
+ *   prec  TOR_PREC_FP64, TOR_PREC_DD, TOR_PREC_FX128, or TOR_PREC_AUTO: the
+ *         FP32 bound pass of tor_bounds picks the starting tier for relative
+ *         tolerance `tol`; while the result's a-posteriori bound err_est
+ *         exceeds tol * |Tor| it is recomputed one tier up (FP64 -> FX128
+ *         when t_max <= 2^11, else double-double; FX128 -> double-double),
+ *         and if double-double still misses, the call returns TOR_EPREC with
+ *         the result filled in.  `tol` is ignored for the explicit tiers.
  *   out   host result; the call synchronises `stream`.
  * The 2^k subsets are split into equal prefix chunks (the high modes of the
  * subset mask fixed per chunk, Algorithm 1's balanced partition) walked
@@ -191,14 +192,17 @@ int tor_fixed_to_result(const uint64_t *limbs8, int k, int tier, tor_result *out
  * reserved, so the whole call can be captured in a CUDA graph.
  *   O     dev  array of n device pointers (each 2k_i x 2k_i FP64, `layout`).
  *   k,ld  dev  arrays of n ints.
- *   prec  TOR_PREC_FP64, TOR_PREC_DD, or TOR_PREC_AUTO (per-instance tier from
- *         the bound pass; FP64 results whose err_est exceeds tol * |Tor| are
- *         recomputed in double-double; results still above get status
- *         TOR_EPREC).
+ *   prec  TOR_PREC_FP64, TOR_PREC_DD, TOR_PREC_FX128 (instances outside the
+ *         fixed-point range get TOR_EINVAL), or TOR_PREC_AUTO (per-instance
+ *         tier from the bound pass; results whose err_est exceeds
+ *         tol * |Tor| are recomputed one tier up as in tor_single, in up to
+ *         two more rounds; results still above get status TOR_EPREC).
  *   out   dev  n results; per-instance status TOR_OK, TOR_ENOTPD, TOR_EPREC,
- *         or TOR_EINVAL (k outside [0, k_max] of the reservation).
- * Without a prior tor_batch_reserve covering n (or when n grows), the call
- * reads k to the host once to size the workspace and synchronises `stream`.
+ *         or TOR_EINVAL (k outside [0, TOR_MAX_K], or above the k_max of an
+ *         explicit tor_batch_reserve).
+ * Without an explicit tor_batch_reserve, every call reads k to the host to
+ * size (and grow) the workspace, which synchronises `stream`.  After one, a
+ * call allocates nothing unless n exceeds its n_max.
  */
 int tor_batch(tor_ctx *ctx, const double *const *O, const int *k, const int *ld, int n,
               int layout, int prec, double tol, cudaStream_t stream, tor_result *out);
@@ -219,7 +223,9 @@ int tor_batch_patterns(tor_ctx *ctx, const double *O, int M, int ld, const uint6
                        int prec, double tol, cudaStream_t stream, tor_result *out);
 
 /* Size the batch workspace for up to n_max instances of at most k_max clicks
- * (allocates; call before capturing tor_batch in a CUDA graph). */
+ * (allocates; call before capturing tor_batch in a CUDA graph).  From then on
+ * tor_batch trusts the reservation: no host reads, instances with k > k_max
+ * get status TOR_EINVAL. */
 int tor_batch_reserve(tor_ctx *ctx, int n_max, int k_max);
 
 /*
@@ -232,8 +238,10 @@ int tor_batch_reserve(tor_ctx *ctx, int n_max, int k_max);
  * Cholesky; bits_needed = log2 kappa_est + log2(4k) + log2(1/tol); tier =
  * TOR_PREC_FP64 if bits_needed <= 72 (FP64's 52 bits plus 20 bits of slack
  * for the estimate's pessimism; AUTO callers verify the result's
- * a-posteriori bound and escalate), else TOR_PREC_DD.  B not positive definite in
- * FP32 gives bits_needed = +inf and tier TOR_PREC_DD.  An instance with k
+ * a-posteriori bound and escalate), else TOR_PREC_FX128 if t_max <= 2^11 and
+ * bits_needed <= 120 (the fixed-point unit's 100 bits plus the same slack),
+ * else TOR_PREC_DD.  B not positive definite in FP32 gives bits_needed = +inf
+ * and tier TOR_PREC_DD.  An instance with k
  * outside [0, TOR_MAX_K] or a null matrix gets tier 0 and NaN fields.
  * The estimates are heuristic: on Haar-mixed lossy GBS states kappa_est
  * over-estimates the true condition number by 10^2 to 10^13.

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <new>
 #include <cstdlib>
+#include <cmath>
 #include "tor_internal.h"
 #include "tor_walk.cuh"
 
@@ -52,13 +53,14 @@ struct tor_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // batch workspace (tor_batch_reserve)
   int batch_nmax = 0, batch_kmax = -1;
+  bool batch_explicit = false;  // sized by the caller's tor_batch_reserve: never re-read k
   Buf batch, batch_scratch;
   tor::BatchPlan plan{};
   tor_bound *bounds_dev = nullptr;
   unsigned char *r1_table_dev = nullptr;
   int *k_dev = nullptr;  // pattern mode: click counts
   Buf mh;                // sampler: proposals, their log q, their Torontonians
-  unsigned char r1_table[3][65];  // walked modes per chunk, by tier and k
+  unsigned char r1_table[4][65];  // walked modes per chunk, by tier (TOR_PREC_*) and k
   // autotuned single-instance settings by tier and k (-1: not tuned)
   signed char tuned_d[4][65];   // by tier (TOR_PREC_FP64 .. TOR_PREC_FX128) and k
   signed char tuned_bps[4][65];
@@ -104,16 +106,57 @@ int check_common(tor_ctx *ctx, const void *O, int k, int ld, int layout) {
   return TOR_OK;
 }
 
-// enqueue prep + walk over chunks [c0, c1); block partials in ctx->block_part
-int enqueue_walk(tor_ctx *ctx, const double *O, int k, int ld, int layout, int tier, int d,
-                 unsigned long long c0, unsigned long long c1, unsigned long long *chunk_part,
-                 cudaStream_t s, int *grid_out) {
+// threads of the walk grid: every block must be resident at once, because
+// chunks are dealt out by a grid stride and a block that waited for a free SM
+// would double the time
+int walk_grid(tor_ctx *ctx, int tier) {
+  const int occ = tor::dfs_max_blocks_per_sm(tier, ctx->threads_per_block);
+  return ctx->sms * (ctx->blocks_per_sm < occ ? ctx->blocks_per_sm : occ);
+}
+
+#ifndef TOR_TAIL_SPLIT
+#define TOR_TAIL_SPLIT 1
+#endif
+
+// Segments for all 2^d chunks on T threads.  The chunks are equal in cost, so
+// the grid-stride loop takes ceil(2^d / T) rounds and a partial last round
+// leaves threads idle.  Only the full rounds W = floor(2^d / T) stay at d
+// bits; the R leftover chunks are cut e bits finer (2^e sub-chunks each, e
+// from a cost model) and walked as a second segment by the whole grid.  The
+// sub-chunks cover the same subsets as their parent chunk; only the rounding
+// of their terms changes, because each root eliminates e more modes before
+// the walk starts.
+tor::WalkSegs plan_segments(int k, int d, size_t T) {
   const int r1 = k - d;
+  const unsigned long long n = 1ull << d;
+  const unsigned long long W = n / T, R = n - W * T;
+  if (!TOR_TAIL_SPLIT || W == 0 || R == 0 || r1 < 2) return tor::one_segment(r1, 0ull, n);
+  // cost of one chunk of r low modes, in FMAs: 27.5 per walked subset plus the
+  // root, about 2 m^2 for each of the k - r fixed modes (half are eliminated)
+  auto cost = [k](int r) {
+    double root = 0.0;
+    for (int m = r; m < k; ++m) root += 2.0 * m * m;
+    return 27.5 * std::ldexp(1.0, r) + root;
+  };
+  int best_e = 0;
+  double best = cost(r1);  // e = 0: one more full-size round
+  for (int e = 1; e <= 3 && e < r1; ++e) {
+    const double rounds = std::ceil((double)(R << e) / (double)T);
+    const double c = rounds * cost(r1 - e);
+    if (c < best) { best = c; best_e = e; }
+  }
+  if (best_e == 0) return tor::one_segment(r1, 0ull, n);
+  tor::WalkSegs g;
+  g.r1[0] = r1;       g.c0[0] = 0ull;                g.c1[0] = W * T;
+  g.r1[1] = r1 - best_e; g.c0[1] = (W * T) << best_e; g.c1[1] = n << best_e;
+  return g;
+}
+
+// enqueue prep + walk over the segments; block partials in ctx->block_part
+int enqueue_walk(tor_ctx *ctx, const double *O, int k, int ld, int layout, int tier, const tor::WalkSegs &seg,
+                 unsigned long long *chunk_part, cudaStream_t s, int grid) {
   const int block = ctx->threads_per_block;
-  // every block of the grid must be resident at once: chunks are dealt out by
-  // a grid stride, so a block that waited for a free SM would double the time
-  const int occ = tor::dfs_max_blocks_per_sm(tier, block);
-  const int grid = ctx->sms * (ctx->blocks_per_sm < occ ? ctx->blocks_per_sm : occ);
+  const int r1 = seg.r1[0];  // the larger of the two
   const size_t nthreads = (size_t)grid * block;
   int rc;
   if ((rc = ensure(ctx, ctx->B, sizeof(double) * 4 * (size_t)k * k))) return rc;
@@ -125,7 +168,7 @@ int enqueue_walk(tor_ctx *ctx, const double *O, int k, int ld, int layout, int t
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(ctx->status.p, 0, sizeof(int), s));
   if (ctx->timing) CK(cudaEventRecord(ctx->ev0, s));
-  tor::launch_dfs(tier, grid, block, (const double *)ctx->B.p, (const double *)ctx->Blo.p, k, r1, c0, c1,
+  tor::launch_dfs(tier, grid, block, (const double *)ctx->B.p, (const double *)ctx->Blo.p, k, seg,
                   (double *)ctx->scratch.p, (unsigned long long *)ctx->block_part.p, chunk_part,
                   (int *)ctx->status.p, s);
   CK(cudaGetLastError());
@@ -133,7 +176,6 @@ int enqueue_walk(tor_ctx *ctx, const double *O, int k, int ld, int layout, int t
     CK(cudaEventRecord(ctx->ev1, s));
     ctx->timed = true;
   }
-  *grid_out = grid;
   return TOR_OK;
 }
 
@@ -164,6 +206,7 @@ int tor_create(tor_ctx **out, int device) {
     c->r1_table[0][kk] = 0;
     c->r1_table[TOR_PREC_FP64][kk] = (unsigned char)(kk < 14 ? kk : 14);
     c->r1_table[TOR_PREC_DD][kk] = (unsigned char)(kk < 12 ? kk : 12);
+    c->r1_table[TOR_PREC_FX128][kk] = (unsigned char)(kk < 12 ? kk : 12);
   }
   cudaError_t e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess) {
@@ -241,11 +284,12 @@ int tor_single_async(tor_ctx *ctx, const double *O, int k, int ld, int layout, i
     return TOR_OK;
   }
   const int d = choose_chunk_bits(ctx, k, prec);
-  int grid = 0;
   const int bps_saved = ctx->blocks_per_sm;
   if (ctx->chunk_bits < 0 && ctx->tuned_bps[prec][k] > 0) ctx->blocks_per_sm = ctx->tuned_bps[prec][k];
-  rc = enqueue_walk(ctx, O, k, ld, layout, prec, d, 0ull, 1ull << d, nullptr, s, &grid);
+  const int grid = walk_grid(ctx, prec);
   ctx->blocks_per_sm = bps_saved;
+  const tor::WalkSegs seg = plan_segments(k, d, (size_t)grid * ctx->threads_per_block);
+  rc = enqueue_walk(ctx, O, k, ld, layout, prec, seg, nullptr, s, grid);
   if (rc) return rc;
   tor::launch_finalize((const unsigned long long *)ctx->block_part.p, grid, k, prec,
                        (const int *)ctx->status.p, out_dev, nullptr, s);
@@ -284,6 +328,7 @@ int tor_single(tor_ctx *ctx, const double *O, int k, int ld, int layout, int pre
       return fail(TOR_EINVAL, "instance outside the 128-bit fixed-point range (log2 t_max = %.2f > %.0f)",
                   (double)bd.log_tmax / 0.6931472, (double)tor::FX128_MAX_LOG2_TMAX);
   }
+  bool fx_ok = false;  // t_max inside the fixed-point range
   if (prec == TOR_PREC_AUTO) {
     if (!(tol > 0.0)) return fail(TOR_EINVAL, "TOR_PREC_AUTO needs a tolerance tol > 0");
     tier = TOR_PREC_FP64;
@@ -295,25 +340,24 @@ int tor_single(tor_ctx *ctx, const double *O, int k, int ld, int layout, int pre
       tor_bound bd;
       CK(cudaMemcpyAsync(&bd, ctx->bound.p, sizeof(bd), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      tier = (bd.tier == TOR_PREC_FP64) ? TOR_PREC_FP64 : TOR_PREC_DD;
+      tier = bd.tier;
+      fx_ok = bd.log_tmax <= tor::FX128_MAX_LOG2_TMAX * 0.6931472f;
     }
   }
-  if ((rc = single_sync(ctx, O, k, ld, layout, tier, s, out))) return rc;
-  if (out->status != TOR_OK)
-    return fail(out->status, "instance status %d (%s)", out->status,
-                out->status == TOR_ENOTPD ? "some I - O_Z is not positive definite" : "term out of range");
-  if (prec == TOR_PREC_AUTO) {
+  while (true) {
+    if ((rc = single_sync(ctx, O, k, ld, layout, tier, s, out))) return rc;
+    if (out->status != TOR_OK)
+      return fail(out->status, "instance status %d (%s)", out->status,
+                  out->status == TOR_ENOTPD ? "some I - O_Z is not positive definite" : "term out of range");
+    if (prec != TOR_PREC_AUTO) return TOR_OK;
     const double mag = out->hi < 0 ? -out->hi : out->hi;
-    if (tier == TOR_PREC_FP64 && out->err_est > tol * mag) {  // a-posteriori escalation
-      tier = TOR_PREC_DD;
-      if ((rc = single_sync(ctx, O, k, ld, layout, tier, s, out))) return rc;
-    }
-    const double mag2 = out->hi < 0 ? -out->hi : out->hi;
-    if (out->err_est > tol * mag2)
+    if (out->err_est <= tol * mag) return TOR_OK;
+    if (tier == TOR_PREC_DD)
       return fail(TOR_EPREC, "error bound %.3e exceeds tol * |Tor| = %.3e even in double-double",
-                  out->err_est, tol * mag2);
+                  out->err_est, tol * mag);
+    // a-posteriori escalation, one tier up
+    tier = (tier == TOR_PREC_FP64 && fx_ok) ? TOR_PREC_FX128 : TOR_PREC_DD;
   }
-  return TOR_OK;
 }
 
 int tor_chunks(tor_ctx *ctx, const double *O, int k, int ld, int layout, int prec, int chunk_bits,
@@ -331,9 +375,8 @@ int tor_chunks(tor_ctx *ctx, const double *O, int k, int ld, int layout, int pre
                                                      (unsigned long long)nchunks);
   if (c_begin == c_end) return TOR_OK;
   CK(cudaSetDevice(ctx->device));
-  int grid = 0;
-  return enqueue_walk(ctx, O, k, ld, layout, prec, chunk_bits, c_begin, c_end,
-                      (unsigned long long *)part_dev, s, &grid);
+  return enqueue_walk(ctx, O, k, ld, layout, prec, tor::one_segment(k - chunk_bits, c_begin, c_end),
+                      (unsigned long long *)part_dev, s, walk_grid(ctx, prec));
 }
 
 int tor_fixed_to_result(const uint64_t *limbs8, int k, int tier, tor_result *out) {
@@ -348,17 +391,25 @@ static int batch_grid(const tor_ctx *ctx, int tier, bool patterns = false) {
   return ctx->sms * (ctx->blocks_per_sm < occ ? ctx->blocks_per_sm : occ);
 }
 
+static int batch_reserve(tor_ctx *ctx, int n_max, int k_max);
+
 int tor_batch_reserve(tor_ctx *ctx, int n_max, int k_max) {
   if (!ctx) return fail(TOR_EINVAL, "null context");
+  const int rc = batch_reserve(ctx, n_max, k_max);
+  if (rc == TOR_OK) ctx->batch_explicit = true;
+  return rc;
+}
+
+static int batch_reserve(tor_ctx *ctx, int n_max, int k_max) {
   if (n_max < 1) return fail(TOR_EINVAL, "n_max = %d < 1", n_max);
   if (k_max < 0 || k_max > TOR_MAX_K) return fail(TOR_EINVAL, "k_max = %d outside [0, %d]", k_max, TOR_MAX_K);
   CK(cudaSetDevice(ctx->device));
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t n = (size_t)n_max;
   const size_t sz_tier = al(n), sz_r1 = al(n), sz_esc = al(n), sz_key = al(4 * n), sz_order = al(4 * n),
-               sz_flags = al(4 * n), sz_off = al(8 * (n + 1)), sz_acc = al(64 * n), sz_range = al(32),
-               sz_counter = al(16), sz_counts = al(8), sz_result = al(sizeof(tor_result) * n),
-               sz_bounds = al(sizeof(tor_bound) * n), sz_r1tab = al(3 * 65), sz_k = al(4 * n);
+               sz_flags = al(4 * n), sz_off = al(8 * (n + 1)), sz_acc = al(64 * n), sz_range = al(48),
+               sz_counter = al(24), sz_counts = al(12), sz_result = al(sizeof(tor_result) * n),
+               sz_bounds = al(sizeof(tor_bound) * n), sz_r1tab = al(4 * 65), sz_k = al(4 * n);
   const size_t total = sz_tier + sz_r1 + sz_esc + sz_key + sz_order + sz_flags + sz_off + sz_acc + sz_range +
                        sz_counter + sz_counts + sz_result + sz_bounds + sz_r1tab + sz_k;
   int rc;
@@ -381,9 +432,9 @@ int tor_batch_reserve(tor_ctx *ctx, int n_max, int k_max) {
   ctx->r1_table_dev = b; b += sz_r1tab;
   ctx->k_dev = (int *)b;
   CK(cudaMemcpy(ctx->r1_table_dev, ctx->r1_table, sizeof(ctx->r1_table), cudaMemcpyHostToDevice));
-  // per-thread walk stacks for the largest instance, for either tier
+  // per-thread walk stacks for the largest instance, for any tier
   size_t scratch = 0;
-  for (int tier = TOR_PREC_FP64; tier <= TOR_PREC_DD; ++tier) {
+  for (int tier = TOR_PREC_FP64; tier <= TOR_PREC_FX128; ++tier) {
     int r1max = 0;
     for (int kk = 0; kk <= k_max; ++kk) r1max = ctx->r1_table[tier][kk] > r1max ? ctx->r1_table[tier][kk] : r1max;
     const int g0 = batch_grid(ctx, tier, false), g1 = batch_grid(ctx, tier, true);
@@ -406,7 +457,7 @@ static int batch_enqueue(tor_ctx *ctx, const tor::BatchInput &in, int n, int pre
   const int block = ctx->threads_per_block;
   double *scratch = (double *)ctx->batch_scratch.p;
   const tor_bound *bd = nullptr;
-  if (prec == TOR_PREC_AUTO) {
+  if (prec == TOR_PREC_AUTO || prec == TOR_PREC_FX128) {  // tiers and the fixed-point range check
     const int rc = pat ? tor::launch_bounds_patterns(in.Ofull, in.M, in.ldfull, in.patterns, in.words, n, tol,
                                                      ctx->bounds_dev, s)
                        : tor::launch_bounds_batch(in.O, in.k, in.ld, n, in.layout, tol, ctx->bounds_dev, s);
@@ -416,18 +467,26 @@ static int batch_enqueue(tor_ctx *ctx, const tor::BatchInput &in, int n, int pre
   const int kmax = (kcap >= 0 && kcap < ctx->batch_kmax) ? kcap : ctx->batch_kmax;
   if (tor::launch_batch_plan(in.k, bd, n, prec, kmax, ctx->r1_table_dev, 0, tol, p, s))
     return fail(TOR_ECUDA, "plan: %s", cudaGetErrorString(cudaGetLastError()));
-  for (int tier = TOR_PREC_FP64; tier <= TOR_PREC_DD; ++tier) {
+  for (int tier = TOR_PREC_FP64; tier <= TOR_PREC_FX128; ++tier) {
     if (prec != TOR_PREC_AUTO && prec != tier) continue;
     if (tor::launch_batch_walk(tier, batch_grid(ctx, tier, pat), block, in, p, scratch, s))
       return fail(TOR_ECUDA, "walk: %s", cudaGetErrorString(cudaGetLastError()));
   }
   if (tor::launch_batch_finalize(in.k, n, 0, 0.0, p, out, s))
     return fail(TOR_ECUDA, "finalize: %s", cudaGetErrorString(cudaGetLastError()));
-  if (prec == TOR_PREC_AUTO) {  // second round: FP64 results that miss tol are redone in double-double
-    if (tor::launch_batch_plan(in.k, bd, n, prec, kmax, ctx->r1_table_dev, 1, tol, p, s) ||
-        tor::launch_batch_walk(TOR_PREC_DD, batch_grid(ctx, TOR_PREC_DD, pat), block, in, p, scratch, s) ||
-        tor::launch_batch_finalize(in.k, n, 0, tol, p, out, s))
-      return fail(TOR_ECUDA, "AUTO second round: %s", cudaGetErrorString(cudaGetLastError()));
+  if (prec == TOR_PREC_AUTO) {
+    // results that miss tol go one tier up: FP64 -> fixed point (in range) or
+    // double-double, then fixed point -> double-double; the last finalize
+    // marks what still misses tol with TOR_EPREC
+    for (int round = 1; round <= 2; ++round) {
+      if (tor::launch_batch_plan(in.k, bd, n, prec, kmax, ctx->r1_table_dev, 1, tol, p, s))
+        return fail(TOR_ECUDA, "AUTO round %d plan: %s", round, cudaGetErrorString(cudaGetLastError()));
+      for (int tier = (round == 1) ? TOR_PREC_FX128 : TOR_PREC_DD; tier >= TOR_PREC_DD; --tier)
+        if (tor::launch_batch_walk(tier, batch_grid(ctx, tier, pat), block, in, p, scratch, s))
+          return fail(TOR_ECUDA, "AUTO round %d walk: %s", round, cudaGetErrorString(cudaGetLastError()));
+      if (tor::launch_batch_finalize(in.k, n, round == 1 ? 1 : 0, round == 1 ? 0.0 : tol, p, out, s))
+        return fail(TOR_ECUDA, "AUTO round %d finalize: %s", round, cudaGetErrorString(cudaGetLastError()));
+    }
   }
   return TOR_OK;
 }
@@ -443,14 +502,14 @@ static int batch_autoreserve(tor_ctx *ctx, const int *k_dev, int n, cudaStream_t
     if (hk[i] > kmax && hk[i] <= TOR_MAX_K) kmax = hk[i];
   delete[] hk;
   if (e != cudaSuccess) return fail(TOR_ECUDA, "reading k: %s", cudaGetErrorString(e));
-  return tor_batch_reserve(ctx, n > ctx->batch_nmax ? n : ctx->batch_nmax, kmax);
+  if (n <= ctx->batch_nmax && kmax <= ctx->batch_kmax) return TOR_OK;
+  return batch_reserve(ctx, n > ctx->batch_nmax ? n : ctx->batch_nmax, kmax);
 }
 
 static int batch_check(tor_ctx *ctx, int n, int prec, double tol) {
   if (!ctx) return fail(TOR_EINVAL, "null context");
   if (n < 0) return fail(TOR_EINVAL, "n = %d < 0", n);
-  if (prec == TOR_PREC_FX128) return fail(TOR_EINVAL, "batches run FP64, DD or AUTO; FX128 is single-instance");
-  if (prec != TOR_PREC_AUTO && prec != TOR_PREC_FP64 && prec != TOR_PREC_DD)
+  if (prec != TOR_PREC_AUTO && prec != TOR_PREC_FP64 && prec != TOR_PREC_DD && prec != TOR_PREC_FX128)
     return fail(TOR_EINVAL, "bad precision %d", prec);
   if (prec == TOR_PREC_AUTO && !(tol > 0.0)) return fail(TOR_EINVAL, "TOR_PREC_AUTO needs tol > 0");
   return TOR_OK;
@@ -464,7 +523,9 @@ int tor_batch(tor_ctx *ctx, const double *const *O, const int *k, const int *ld,
   if (!O || !k || !ld || !out) return fail(TOR_EINVAL, "null array pointer");
   if (layout != TOR_LAYOUT_XXPP && layout != TOR_LAYOUT_XPXP) return fail(TOR_EINVAL, "bad layout %d", layout);
   CK(cudaSetDevice(ctx->device));
-  if (n > ctx->batch_nmax || ctx->batch_kmax < 0)
+  // without an explicit reservation every call sizes the workspace for its own
+  // k (one host read), so no instance is refused for outgrowing an earlier call
+  if (!ctx->batch_explicit || n > ctx->batch_nmax)
     if ((rc = batch_autoreserve(ctx, k, n, s))) return rc;
   tor::BatchInput in{O, k, ld, layout, nullptr, nullptr, 0, 0, 0};
   return batch_enqueue(ctx, in, n, prec, tol, s, out);
@@ -484,8 +545,8 @@ static int batch_patterns(tor_ctx *ctx, const double *O, int M, int ld, const ui
   // once, so that no later pattern is refused for outgrowing an earlier batch
   const int kstate = M < TOR_MAX_K ? M : TOR_MAX_K;
   if (n > ctx->batch_nmax || ctx->batch_kmax < kstate)
-    if ((rc = tor_batch_reserve(ctx, n > ctx->batch_nmax ? n : ctx->batch_nmax,
-                                kstate > ctx->batch_kmax ? kstate : ctx->batch_kmax)))
+    if ((rc = batch_reserve(ctx, n > ctx->batch_nmax ? n : ctx->batch_nmax,
+                            kstate > ctx->batch_kmax ? kstate : ctx->batch_kmax)))
       return rc;
   if (tor::launch_pattern_popcount((const unsigned long long *)patterns, n, words, ctx->k_dev, s))
     return fail(TOR_ECUDA, "popcount: %s", cudaGetErrorString(cudaGetLastError()));

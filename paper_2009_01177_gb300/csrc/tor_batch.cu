@@ -22,8 +22,11 @@
 //                    warp ran which item.
 //  k_batch_finalize  one thread per instance: accumulator -> tor_result.
 //
-// In TOR_PREC_AUTO mode a second plan/walk/finalize round re-runs in
-// double-double every instance whose FP64 result misses the tolerance.
+// Three tiers share the item axis in the order FP64, double-double, 128-bit
+// fixed point.  In TOR_PREC_AUTO mode up to two more plan/walk/finalize
+// rounds re-run every instance whose result misses the tolerance one tier up:
+// FP64 -> fixed point (when t_max fits its range) or double-double, then
+// fixed point -> double-double.
 #include <cuda_runtime.h>
 #include <cstdint>
 #include "tor_dfs.cuh"
@@ -33,7 +36,11 @@
 namespace tor {
 
 constexpr int PLAN_THREADS = 1024;
-constexpr int NKEY = 2 * 65;  // (tier 1|2) x (64 - r1)
+constexpr int NKEY = 3 * 65;  // (tier 1|2|3) x (64 - r1)
+
+__device__ __forceinline__ bool fx_in_range(const tor_bound &b) {
+  return b.log_tmax <= FX128_MAX_LOG2_TMAX * 0.6931472f;
+}
 
 // acc (4 limbs) += X, exactly modulo 2^256, from any number of threads
 __device__ __forceinline__ void fx_atomic_add(unsigned long long *acc, const Fx256 &X) {
@@ -51,10 +58,12 @@ __device__ __forceinline__ void fx_atomic_add(unsigned long long *acc, const Fx2
   }
 }
 
-// mode 0: first round; mode 1: escalate failed FP64 instances to double-double
+// mode 0: first round; mode 1: escalate the instances that missed tol one tier
+// up (FP64 -> fixed point when in range, else double-double; fixed point ->
+// double-double); bounds is needed for AUTO and for an explicit FX128 batch
 __global__ void __launch_bounds__(PLAN_THREADS)
 k_batch_plan(const int *__restrict__ k, const tor_bound *__restrict__ bounds, int n, int prec, int kmax,
-             const unsigned char *__restrict__ r1_table /* [3][65] */, int mode, double tol,
+             const unsigned char *__restrict__ r1_table /* [4][65] */, int mode, double tol,
              BatchPlan p) {
   __shared__ unsigned int hist[NKEY], cursor[NKEY];
   __shared__ unsigned long long part[PLAN_THREADS];
@@ -68,6 +77,7 @@ k_batch_plan(const int *__restrict__ k, const tor_bound *__restrict__ bounds, in
     if (mode == 0) {
       tier = (prec == TOR_PREC_AUTO) ? (bounds ? bounds[i].tier : TOR_PREC_FP64) : prec;
       if (ki < 0 || ki > kmax) tier = 0;
+      if (tier == TOR_PREC_FX128 && ki > 0 && !(bounds && fx_in_range(bounds[i]))) tier = 0;
       p.tier[i] = (unsigned char)tier;
       p.flags[i] = (tier == 0) ? ST_RANGE : 0;
       p.escalated[i] = 0;
@@ -75,10 +85,15 @@ k_batch_plan(const int *__restrict__ k, const tor_bound *__restrict__ bounds, in
       tier = 0;
       const tor_result r = p.result[i];
       const double mag = r.hi < 0 ? -r.hi : r.hi;
-      if (p.tier[i] == TOR_PREC_FP64 && r.status == TOR_OK && r.err_est > tol * mag) {
-        tier = TOR_PREC_DD;
-        p.tier[i] = TOR_PREC_DD;
-        p.escalated[i] = 1;
+      if (r.status == TOR_OK && r.err_est > tol * mag) {
+        if (p.tier[i] == TOR_PREC_FP64)
+          tier = (bounds && ki > 0 && fx_in_range(bounds[i])) ? TOR_PREC_FX128 : TOR_PREC_DD;
+        else if (p.tier[i] == TOR_PREC_FX128)
+          tier = TOR_PREC_DD;
+      }
+      p.escalated[i] = (tier != 0) ? 1 : 0;
+      if (tier != 0) {
+        p.tier[i] = (unsigned char)tier;
         p.flags[i] = 0;
       }
     }
@@ -101,10 +116,11 @@ k_batch_plan(const int *__restrict__ k, const tor_bound *__restrict__ bounds, in
   __syncthreads();
   if (tid == 0) {
     unsigned int run = 0;
-    for (int e = 0; e < NKEY; ++e) { cursor[e] = run; run += hist[e]; }
-    p.counts[0] = 0;
-    for (int e = 0; e < 65; ++e) p.counts[0] += hist[e];  // FP64 instances
-    p.counts[1] = run;                                    // all scheduled instances
+    for (int e = 0; e < NKEY; ++e) {
+      cursor[e] = run;
+      run += hist[e];
+      if (e % 65 == 64) p.counts[e / 65] = run;  // instances of tiers <= e / 65 + 1
+    }
   }
   __syncthreads();
   // phase 2: scatter into sorted order
@@ -114,7 +130,7 @@ k_batch_plan(const int *__restrict__ k, const tor_bound *__restrict__ bounds, in
   }
   __syncthreads();
   // phase 3: exclusive scan of chunk counts over the sorted order
-  const int m = (int)p.counts[1];
+  const int m = (int)p.counts[2];
   const int per = (m + PLAN_THREADS - 1) / PLAN_THREADS;
   const int lo = tid * per, hi = min(m, lo + per);
   unsigned long long sum = 0;
@@ -139,30 +155,28 @@ k_batch_plan(const int *__restrict__ k, const tor_bound *__restrict__ bounds, in
   }
   if (tid == PLAN_THREADS - 1) p.item_off[m] = run;
   __syncthreads();
-  if (tid == 0) {
-    const unsigned long long split = p.item_off[p.counts[0]];
-    p.range[0] = 0ull;       // FP64 items [0, split)
-    p.range[1] = split;
-    p.range[2] = split;      // double-double items [split, total)
-    p.range[3] = p.item_off[m];
-    p.counter[0] = p.range[0];
-    p.counter[1] = p.range[2];
+  if (tid == 0) {  // items of tier t + 1: [range[2t], range[2t + 1])
+    for (int t = 0; t < 3; ++t) {
+      p.range[2 * t] = (t == 0) ? 0ull : p.item_off[p.counts[t - 1]];
+      p.range[2 * t + 1] = p.item_off[p.counts[t]];
+      p.counter[t] = p.range[2 * t];
+    }
   }
 }
 
 template <class Tier, bool PAT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, Tier::MINB)
 k_batch_walk(BatchInput in, BatchPlan p, double *__restrict__ scratch) {
   extern __shared__ double smem[];
   double *Q = smem + threadIdx.x;
-  constexpr int t = (Tier::W == 1) ? 0 : 1;
+  constexpr int t = Tier::PREC - 1;
   const size_t st = (size_t)gridDim.x * blockDim.x;
   const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   double *S = scratch + gtid;
   const int lane = threadIdx.x & 31;
   const unsigned long long end = p.range[2 * t + 1];
-  const int jlo = (t == 0) ? 0 : (int)p.counts[0];
-  const int jhi = (t == 0) ? (int)p.counts[0] : (int)p.counts[1];
+  const int jlo = (t == 0) ? 0 : (int)p.counts[t - 1];
+  const int jhi = (int)p.counts[t];
   while (true) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(p.counter + t, 32ull);
@@ -233,6 +247,11 @@ int launch_batch_walk(int tier, int grid, int block, const BatchInput &in, const
     const size_t sm = walk_smem_bytes<TierDD>(block);
     if (pat) k_batch_walk<TierDD, true><<<grid, block, sm, s>>>(in, p, scratch);
     else k_batch_walk<TierDD, false><<<grid, block, sm, s>>>(in, p, scratch);
+  } else if (tier == TOR_PREC_FX128) {
+    using TF = TierFx<FX128_FRAC>;
+    const size_t sm = walk_smem_bytes<TF>(block);
+    if (pat) k_batch_walk<TF, true><<<grid, block, sm, s>>>(in, p, scratch);
+    else k_batch_walk<TF, false><<<grid, block, sm, s>>>(in, p, scratch);
   } else {
     const size_t sm = walk_smem_bytes<TierF64>(block);
     if (pat) k_batch_walk<TierF64, true><<<grid, block, sm, s>>>(in, p, scratch);
@@ -270,6 +289,11 @@ static int occ_of(K kern, int block, size_t sm) {
 }
 
 int batch_walk_max_blocks_per_sm(int tier, int block, bool patterns) {
+  if (tier == TOR_PREC_FX128) {
+    using TF = TierFx<FX128_FRAC>;
+    const size_t sm = walk_smem_bytes<TF>(block);
+    return patterns ? occ_of(k_batch_walk<TF, true>, block, sm) : occ_of(k_batch_walk<TF, false>, block, sm);
+  }
   if (tier == TOR_PREC_DD) {
     const size_t sm = walk_smem_bytes<TierDD>(block);
     return patterns ? occ_of(k_batch_walk<TierDD, true>, block, sm) : occ_of(k_batch_walk<TierDD, false>, block, sm);

@@ -21,17 +21,17 @@ constexpr float FX128_MAX_LOG2_TMAX = 11.0f;
 
 // device arrays of a batch plan (sized for n_max instances by tor_batch_reserve)
 struct BatchPlan {
-  unsigned char *tier;            // n: 0 = not scheduled (invalid), TOR_PREC_FP64, TOR_PREC_DD
+  unsigned char *tier;            // n: 0 = not scheduled (invalid), else TOR_PREC_FP64 | DD | FX128
   unsigned char *r1;              // n: walked (low) modes per chunk
-  unsigned char *escalated;       // n: re-run in double-double by the AUTO second round
+  unsigned char *escalated;       // n: re-run one tier up by the current AUTO round
   int *key;                       // n: sort key, -1 = not scheduled
   int *order;                     // n: instances sorted by (tier, r1 descending)
   int *flags;                     // n: ST_* status bits
   unsigned long long *item_off;   // n + 1: exclusive scan of chunk counts in sorted order
   unsigned long long *acc;        // n x 8: exact fixed-point sums (signed, abs)
-  unsigned long long *range;      // 4: [fp64 begin, fp64 end, dd begin, dd end) item ranges
-  unsigned long long *counter;    // 2: work counters per tier
-  unsigned int *counts;           // 2: number of FP64 instances, number scheduled
+  unsigned long long *range;      // 6: [begin, end) item range of each tier (FP64, DD, FX128)
+  unsigned long long *counter;    // 3: work counter of each tier
+  unsigned int *counts;           // 3: scheduled instances of tiers <= FP64, <= DD, <= FX128
   tor_result *result;             // n: last finalized results (input of the AUTO round)
 };
 
@@ -58,9 +58,20 @@ int launch_batch_finalize(const int *k, int n, int only_escalated, double tol, c
 int batch_walk_max_blocks_per_sm(int tier, int block, bool patterns);
 
 void launch_prep(const double *O, int k, int ld, int layout, double *B, double *Blo, cudaStream_t s);
-void launch_dfs(int tier, int grid, int block, const double *B, const double *Blo, int k, int r1,
-                unsigned long long c0, unsigned long long c1, double *scratch,
-                unsigned long long *block_part, unsigned long long *chunk_part, int *status,
+// Up to two chunk segments per walk launch: segment 0 walks chunks [c0, c1)
+// of r1 low modes each; segment 1 (empty when c0 == c1) walks finer chunks of
+// a smaller r1.  Every thread takes its grid-stride share of segment 0 and
+// then of segment 1, so a partial last wave of segment 0 can be cut into
+// finer pieces that fill the machine.
+struct WalkSegs {
+  int r1[2];
+  unsigned long long c0[2], c1[2];
+};
+inline WalkSegs one_segment(int r1, unsigned long long c0, unsigned long long c1) {
+  return WalkSegs{{r1, r1}, {c0, 0ull}, {c1, 0ull}};
+}
+void launch_dfs(int tier, int grid, int block, const double *B, const double *Blo, int k, const WalkSegs &seg,
+                double *scratch, unsigned long long *block_part, unsigned long long *chunk_part, int *status,
                 cudaStream_t s);
 void launch_finalize(const unsigned long long *block_part, int nblocks, int k, int tier,
                      const int *status, tor_result *out, unsigned long long *total8, cudaStream_t s);

@@ -37,11 +37,10 @@ __global__ void k_prep(const double *__restrict__ O, int k, int ld, int layout,
 }
 
 template <class Tier>
-__global__ void __launch_bounds__(128)
-k_dfs(const double *__restrict__ B, const double *__restrict__ Blo, int k, int r1,
-      unsigned long long c_begin, unsigned long long c_end, double *__restrict__ scratch,
-      unsigned long long *__restrict__ block_part, unsigned long long *__restrict__ chunk_part,
-      int *__restrict__ status) {
+__global__ void __launch_bounds__(128, Tier::MINB)
+k_dfs(const double *__restrict__ B, const double *__restrict__ Blo, int k, const WalkSegs seg,
+      double *__restrict__ scratch, unsigned long long *__restrict__ block_part,
+      unsigned long long *__restrict__ chunk_part, int *__restrict__ status) {
   extern __shared__ double smem[];
   const size_t st = (size_t)gridDim.x * blockDim.x;
   const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -54,20 +53,23 @@ k_dfs(const double *__restrict__ B, const double *__restrict__ Blo, int k, int r
   fx_zero(tot_sabs);
   int flags = 0;
 
-  for (unsigned long long c = c_begin + gtid; c < c_end; c += st) {
-    Sums Sm;
-    fx_zero(Sm.tor);
-    fx_zero(Sm.sabs);
-    Sm.flags = 0;
-    walk_chunk<Tier>(src, k, r1, c, S, st, Sm, Q, blockDim.x);
-    if (chunk_part) {
-      unsigned long long *o = chunk_part + (size_t)(c - c_begin) * 8;
+  for (int g = 0; g < 2; ++g) {
+    const int r1 = seg.r1[g];
+    for (unsigned long long c = seg.c0[g] + gtid; c < seg.c1[g]; c += st) {
+      Sums Sm;
+      fx_zero(Sm.tor);
+      fx_zero(Sm.sabs);
+      Sm.flags = 0;
+      walk_chunk<Tier>(src, k, r1, c, S, st, Sm, Q, blockDim.x);
+      if (chunk_part && g == 0) {
+        unsigned long long *o = chunk_part + (size_t)(c - seg.c0[0]) * 8;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) { o[i] = Sm.tor.w[i]; o[4 + i] = Sm.sabs.w[i]; }
+        for (int i = 0; i < 4; ++i) { o[i] = Sm.tor.w[i]; o[4 + i] = Sm.sabs.w[i]; }
+      }
+      fx_add(tot_tor, Sm.tor);
+      fx_add(tot_sabs, Sm.sabs);
+      flags |= Sm.flags;
     }
-    fx_add(tot_tor, Sm.tor);
-    fx_add(tot_sabs, Sm.sabs);
-    flags |= Sm.flags;
   }
 
   // block reduction (exact, so the order does not matter) in the node slots' memory
@@ -129,23 +131,22 @@ void launch_prep(const double *O, int k, int ld, int layout, double *B, double *
   k_prep<<<(n + 255) / 256, 256, 0, s>>>(O, k, ld, layout, B, Blo);
 }
 
-void launch_dfs(int tier, int grid, int block, const double *B, const double *Blo, int k, int r1,
-                unsigned long long c0, unsigned long long c1, double *scratch,
-                unsigned long long *block_part, unsigned long long *chunk_part, int *status,
+void launch_dfs(int tier, int grid, int block, const double *B, const double *Blo, int k, const WalkSegs &seg,
+                double *scratch, unsigned long long *block_part, unsigned long long *chunk_part, int *status,
                 cudaStream_t s) {
   if (tier == TOR_PREC_DD) {
     const size_t sm = walk_smem_bytes<TierDD>(block);
     cudaFuncSetAttribute(k_dfs<TierDD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_dfs<TierDD><<<grid, block, sm, s>>>(B, Blo, k, r1, c0, c1, scratch, block_part, chunk_part, status);
+    k_dfs<TierDD><<<grid, block, sm, s>>>(B, Blo, k, seg, scratch, block_part, chunk_part, status);
   } else if (tier == TOR_PREC_FX128) {
     using TF = TierFx<FX128_FRAC>;
     const size_t sm = walk_smem_bytes<TF>(block);
     cudaFuncSetAttribute(k_dfs<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_dfs<TF><<<grid, block, sm, s>>>(B, Blo, k, r1, c0, c1, scratch, block_part, chunk_part, status);
+    k_dfs<TF><<<grid, block, sm, s>>>(B, Blo, k, seg, scratch, block_part, chunk_part, status);
   } else {
     const size_t sm = walk_smem_bytes<TierF64>(block);
     cudaFuncSetAttribute(k_dfs<TierF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_dfs<TierF64><<<grid, block, sm, s>>>(B, Blo, k, r1, c0, c1, scratch, block_part, chunk_part, status);
+    k_dfs<TierF64><<<grid, block, sm, s>>>(B, Blo, k, seg, scratch, block_part, chunk_part, status);
   }
 }
 

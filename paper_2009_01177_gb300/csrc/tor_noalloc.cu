@@ -122,8 +122,8 @@ int tor_single_noalloc(const double *O, int k, int ld, int layout, int prec, cud
   tor::launch_prep(O, k, ld, layout, B, Blo, stream);
   e = cudaMemsetAsync(status, 0, sizeof(int), stream);  // the only buffer that must start at zero
   if (e != cudaSuccess) return nfail(TOR_ECUDA, "status clear: %s", cudaGetErrorString(e));
-  tor::launch_dfs(prec, grid, NOALLOC_THREADS, B, Blo, k, r1, 0ull, 1ull << d, stack, part, nullptr,
-                  status, stream);
+  tor::launch_dfs(prec, grid, NOALLOC_THREADS, B, Blo, k, tor::one_segment(r1, 0ull, 1ull << d), stack, part,
+                  nullptr, status, stream);
   tor::launch_finalize(part, grid, k, prec, status, out_dev, nullptr, stream);
   e = cudaGetLastError();
   if (e != cudaSuccess) return nfail(TOR_ECUDA, "launch: %s", cudaGetErrorString(e));

@@ -1,5 +1,6 @@
 """GPU tests of the FP32 bound pass (tor_bounds) and the AUTO precision router."""
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -39,7 +40,8 @@ def test_bounds_match_reference_formulas(ctx):
         ref = reference_bound(O, 1e-10)
         for key in ("log_tmax", "log_tor_est", "log_kappa_est", "bits_needed"):
             assert abs(g[key] - ref[key]) <= 1e-3 * max(1.0, abs(ref[key])), (key, g[key], ref[key])
-        assert g["tier"] == (1 if ref["bits_needed"] <= 72 else 2)
+        fx_ok = ref["log_tmax"] <= 11 * math.log(2) and ref["bits_needed"] <= 120
+        assert g["tier"] == (1 if ref["bits_needed"] <= 72 else (3 if fx_ok else 2))
 
 
 def test_bounds_thermal_are_exact_estimates(ctx):
@@ -76,6 +78,17 @@ def test_auto_meets_tolerance_or_reports(ctx, cuda_lib, tol):
             assert e.code == cuda_lib.TOR_EPREC
             continue
         assert abs((r.hi - ref.hi) + (r.lo - ref.lo)) <= max(r.err_est, 0) <= tol * abs(ref.value) * (1 + 1e-6)
+
+
+def test_auto_uses_fixed_point_between_fp64_and_double_double(ctx):
+    # kappa = 4e15: FP64's bound (64 u kappa = 30) misses 1e-12, fixed point's (2e-13) meets it
+    st, pat, O32 = gi.workload_m100(32)
+    O = gi.select(st.O, pat[:16])
+    ref = oracle.tor(O)
+    r = ctx.single(torch.from_numpy(O).cuda(), prec="auto", tol=1e-12)
+    assert r.tier == 3
+    err = abs(float(Fraction(r.hi) + Fraction(r.lo) - Fraction(ref.hi) - Fraction(ref.lo)))
+    assert err <= r.err_est <= 1e-12 * abs(ref.value)
 
 
 def test_auto_picks_fp64_when_well_conditioned(ctx):

@@ -242,6 +242,27 @@ def test_shard_ranges_gather_to_the_single_result(ctx):
     assert (r_sh.hi, r_sh.lo, r_sh.sum_abs) == (r.hi, r.lo, r.sum_abs)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "dd"])
+def test_tail_split_matches_the_unsplit_chunk_sum(ctx, prec):
+    # 2^18 chunks on the default grid leave a partial last round, which
+    # tor_single cuts into finer sub-chunks: the same subsets, other rounding
+    from paper_2009_01177_gb300 import shard
+    from paper_2009_01177_gb300.tor import fixed_to_result
+    st, pat, O32 = gi.workload_m100(32)
+    k, d = 22, 18
+    Od = dev(gi.select(st.O, pat[:k]))
+    tot = shard.sum_partials(ctx.chunks(Od, d, 0, 1 << d, prec=prec).cpu().numpy().view(np.uint64))
+    r_chunks = fixed_to_result([int(x) for x in tot], k, prec)
+    ctx.set_chunk_bits(d)
+    r = ctx.single(Od, prec=prec)
+    ctx.set_chunk_bits(-1)
+    assert r.status == 0
+    # a missing or doubled sub-chunk would move sum_abs by about 2^-18 of itself
+    assert abs(r.sum_abs - r_chunks.sum_abs) <= 1e-12 * r.sum_abs
+    diff = abs((Fraction(r.hi) + Fraction(r.lo)) - (Fraction(r_chunks.hi) + Fraction(r_chunks.lo)))
+    assert float(diff) <= r.err_est + r_chunks.err_est
+
+
 # ------------------------------------------------------- 128-bit fixed point
 @pytest.mark.parametrize("k", [1, 4, 9, 13])
 def test_fx128_thermal_closed_form(ctx, k):
