@@ -51,6 +51,35 @@ def workload(k, rank):
     return st, pat, O
 
 
+# sources that define the single-instance FP64 walk kernel: a recorded DRAM
+# traffic figure is reported only while they are unchanged
+WALK_SOURCES = ["paper_2009_01177_gb300/csrc/" + f for f in
+                ("tor_dfs.cuh", "tor_walk.cuh", "tor_kernels.cu", "fx128.cuh", "tor_internal.h", "capi.cu")]
+
+
+def walk_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in WALK_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def walk_traffic(k):
+    """DRAM bytes per k_dfs launch from the committed ncu summary, if taken on these sources."""
+    import re
+    path = os.path.join(ROOT, "profiles", f"k_dfs_fp64_k{k}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch = ([0-9.eE+]+) \(walk sources sha256 ([0-9a-f]{64})\)", text)
+    if not m or m.group(2) != walk_sources_sha256():
+        return None
+    return float(m.group(1))
+
+
 def config(k, extra=None):
     c = {"workload": f"single Torontonian k={k} ({2 * k}x{2 * k} FP64 O_S) of a synthetic M=100 lossy "
                      f"GBS state (r~U[0.6,1.2], Haar U, eta=0.3, seed 2)",
@@ -175,6 +204,64 @@ def batch_patterns_m100(n, seed=4, k_lo=8, k_hi=30):
         if k_lo <= x.sum() <= k_hi:
             pats.append(x)
     return st, np.array(pats)
+
+
+def run_adaptive(args):
+    """Adaptive precision: the bound pass routes a k=40 instance of a brighter M=100 state,
+    and timed random windows of chunks at the routed tier project the full k=40 and k=50 runs."""
+    import math
+    import torch
+    from paper_2009_01177_gb300 import gbs_inputs as gi
+    from paper_2009_01177_gb300 import tor
+    ctx = tor.Context(0)
+    st = gi.lossy_gbs_state(100, 0.8, 1.4, 0.3, 3)
+    pat = gi.random_pattern(100, 50, 1003)
+    tol = 1e-10
+    rng = np.random.default_rng(3)
+    # walked modes per chunk: at k >= 40 a chunk's root eliminates 26+ modes, so
+    # longer chunks than the k <= 32 defaults keep the root a few percent of the walk
+    r1_of = {"fp64": 16, "dd": 13, "fx128": 13}
+    window = 1 << 18                      # chunks per timed launch: 3.4 per thread of the grid
+    out = {"metric": "adaptive precision: routed tier and projected single-GPU runtime (k=40, k=50)",
+           "unit": "subset-dets/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+           "config": {"workload": "M=100 synthetic lossy GBS state (r~U[0.8,1.4], Haar U, eta=0.3, seed 3), "
+                                  "nested random patterns of k=40 and k=50 clicks; tol=1e-10",
+                      "window_chunks": window, "l2": "inputs resident (the walk reads a 2k x 2k matrix)"}}
+    with ClockSampler(0) as clocks:
+        for k in (40, 50):
+            Od = torch.from_numpy(gi.select(st.O, pat[:k])).cuda()
+            bd = ctx.bounds([Od], tol=tol)[0]
+            routed = {1: "fp64", 2: "dd", 3: "fx128"}[int(bd["tier"])]
+            rows = {}
+            for prec in dict.fromkeys([routed, "fp64"]):
+                d = k - r1_of[prec]
+                nchunks = 1 << d
+                ms = []
+                for w in range(4):
+                    c0 = int(rng.integers(0, nchunks // window)) * window
+                    if w == 0:                # warm-up window, not timed
+                        ctx.chunks(Od, d, c0, c0 + window, prec=prec)
+                        torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    ctx.chunks(Od, d, c0, c0 + window, prec=prec)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                mean = float(np.mean(ms))
+                rate = window * (1 << (k - d)) / (mean * 1e-3)
+                rows[prec] = {"chunk_bits": d, "windows_ms": [round(x, 2) for x in ms],
+                              "window_cv": float(np.std(ms) / mean), "subset_dets_per_s": rate,
+                              "projected_full_s": float(2.0 ** k / rate)}
+            out[f"k{k}"] = {"routed_tier": routed, "bits_needed": bd["bits_needed"],
+                            "log2_tmax": bd["log_tmax"] / math.log(2),
+                            "log2_kappa_est": bd["log_kappa_est"] / math.log(2), "tiers": rows}
+    out["value"] = out["k40"]["tiers"][out["k40"]["routed_tier"]]["subset_dets_per_s"]
+    out["dtype"] = out["k40"]["routed_tier"]
+    out["clocks"] = clocks.summary()
+    out["paper_context"] = "one k=50 Torontonian: 73,773 s (128-bit) and 170,891 s (256-bit) on 39,286 Sunway TaihuLight nodes"
+    print(json.dumps(out), flush=True)
+    ctx.close()
 
 
 def run_batch(args):
@@ -390,8 +477,11 @@ def main():
     ap.add_argument("--k", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--mode", default="single", choices=["single", "batch", "mh"])
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "mh", "adaptive"])
     ap.add_argument("--n", type=int, default=4096, help="patterns (batch) or chains (mh)")
+    ap.add_argument("--chunk-bits", type=int, default=None,
+                    help="single mode: chunk depth d instead of the autotuner's choice")
+    ap.add_argument("--blocks-per-sm", type=int, default=4, help="with --chunk-bits: resident blocks per SM")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -404,6 +494,9 @@ def main():
         return
     if args.mode == "mh":
         run_mh(args)
+        return
+    if args.mode == "adaptive":
+        run_adaptive(args)
         return
 
     import torch
@@ -420,6 +513,15 @@ def main():
     st, pat, O = workload(k, rank)
     ctx = tor.Context(local)
     peak_dfma, clk = ctx.fp64_peak()
+    if args.chunk_bits is None:
+        # the project's autotuner picks the chunk depth and blocks per SM for this k (about 20 s)
+        tuned_d, tuned_bps = ctx.autotune(k, "fp64")
+        launch_how = "autotuned"
+    else:
+        tuned_d, tuned_bps = args.chunk_bits, args.blocks_per_sm
+        ctx.set_chunk_bits(tuned_d)
+        ctx.set_launch(128, tuned_bps)
+        launch_how = "given"
     Od = torch.from_numpy(O).to(dev)
     out = torch.empty(tor.RESULT_BYTES, dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -479,18 +581,13 @@ def main():
             cpu = {"value": n / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"{nch} random 256-subset chunks (masks [c 2^8, (c+1) 2^8)) of the same "
                              f"k={k} matrix, {el:.1f} s; 256-bit fixed point, OpenMP over masks"}
-        traffic = None
-        prof = os.path.join(ROOT, "profiles", "traffic.json")
-        if os.path.exists(prof):
-            try:
-                traffic = json.load(open(prof)).get(f"k_dfs_fp64_k{k}")
-            except (OSError, ValueError):
-                traffic = None
+        traffic = walk_traffic(k)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config(k, {"fp64_peak_frac": achieved / PEAK_TFLOPS}),
+            "config": config(k, {"fp64_peak_frac": achieved / PEAK_TFLOPS, "chunk_bits": tuned_d,
+                                 "blocks_per_sm": tuned_bps, "launch": launch_how}),
             "e2e": {"value": float(2 ** k) * args.steps * world / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(O.nbytes), "d2h_bytes_per_step": tor.RESULT_BYTES},
             "gpu_launches": 3 * args.steps,

@@ -330,7 +330,7 @@ int tor_walk_time(tor_ctx *ctx, float *ms);
 /*
  * tor_autotune: pick the chunk depth d (walked modes per chunk k - d) and
  * blocks per SM that run fastest for instances of k clicks in tier `prec`,
- * by timing candidates (k - d in {8, 10, 12, 14, 16}, 2-4 blocks per SM) on a
+ * by timing candidates (k - d in {8, 10, 12, 13, 14, 15, 16}, 2-4 blocks per SM) on a
  * synthetic instance of that size (the walk's cost depends only on k).  The
  * choice is kept in the context (used by tor_single when chunk bits are
  * automatic, and by the batch planner for that k) and, if cache_path is not

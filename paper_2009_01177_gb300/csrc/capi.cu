@@ -666,7 +666,9 @@ int tor_autotune(tor_ctx *ctx, int k, int prec, const char *cache_path, int *chu
       if (found) {
         ctx->tuned_d[prec][k] = (signed char)best.d;
         ctx->tuned_bps[prec][k] = (signed char)best.bps;
-        if (prec <= TOR_PREC_DD) ctx->r1_table[prec][k] = (unsigned char)(k - best.d);
+        ctx->r1_table[prec][k] = (unsigned char)(k - best.d);
+        if (ctx->r1_table_dev)  // the batch plan reads the device copy
+          CK(cudaMemcpy(ctx->r1_table_dev, ctx->r1_table, sizeof(ctx->r1_table), cudaMemcpyHostToDevice));
         if (chunk_bits_out) *chunk_bits_out = best.d;
         if (blocks_per_sm_out) *blocks_per_sm_out = best.bps;
         return TOR_OK;
@@ -693,7 +695,7 @@ int tor_autotune(tor_ctx *ctx, int k, int prec, const char *cache_path, int *chu
   const int saved_d = ctx->chunk_bits, saved_bps = ctx->blocks_per_sm;
   double best_ms = 1e30;
   int best_d = choose_chunk_bits(ctx, k), best_bps = saved_bps;
-  const int r1s[] = {8, 10, 12, 14, 16};
+  const int r1s[] = {8, 10, 12, 13, 14, 15, 16};
   const int bpss[] = {2, 3, 4};
   int rc = TOR_OK;
   for (int r1 : r1s) {
@@ -728,7 +730,7 @@ int tor_autotune(tor_ctx *ctx, int k, int prec, const char *cache_path, int *chu
   if (rc) return rc;
   ctx->tuned_d[prec][k] = (signed char)best_d;
   ctx->tuned_bps[prec][k] = (signed char)best_bps;
-  if (prec <= TOR_PREC_DD) ctx->r1_table[prec][k] = (unsigned char)(k - best_d);
+  ctx->r1_table[prec][k] = (unsigned char)(k - best_d);
   if (ctx->r1_table_dev)
     CK(cudaMemcpy(ctx->r1_table_dev, ctx->r1_table, sizeof(ctx->r1_table), cudaMemcpyHostToDevice));
   if (cache_path) {

@@ -53,6 +53,7 @@ k_dfs(const double *__restrict__ B, const double *__restrict__ Blo, int k, const
   fx_zero(tot_sabs);
   int flags = 0;
 
+#pragma unroll 1
   for (int g = 0; g < 2; ++g) {
     const int r1 = seg.r1[g];
     for (unsigned long long c = seg.c0[g] + gtid; c < seg.c1[g]; c += st) {
