@@ -133,6 +133,30 @@ def test_sharded_chunks_add_up_exactly(ctx):
     assert (r_sh.hi, r_sh.lo) == (r.hi, r.lo)
 
 
+_K32_CHUNK_REF = {}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "dd", "fx128"])
+def test_k32_sampled_chunks_at_bench_depth(ctx, prec):
+    # the benchmark's instance at its autotuned chunk depth (d = 16: 2^16 chunks of 2^16
+    # subsets): one chunk with none of the 16 fixed modes in Z and one with all of them
+    # (64 x 64 determinants), each against the oracle's own mask range
+    from paper_2009_01177_gb300.tor import limbs_to_int
+    st, pat, O = gi.workload_m100(32)
+    Od = dev(O)
+    k, d = 32, 16
+    u = {"fp64": 2.0 ** -53, "dd": 2.0 ** -104, "fx128": 2.0 ** -100}[prec]
+    for c in (0x0000, 0xFFFF):
+        if c not in _K32_CHUNK_REF:
+            _K32_CHUNK_REF[c] = oracle.tor_range(O, c << (k - d), (c + 1) << (k - d))
+        ref = _K32_CHUNK_REF[c]
+        part = ctx.chunks(Od, d, c, c + 1, prec=prec).cpu().numpy()[0]
+        got = Fraction(limbs_to_int(part[:4]), 1 << 128)
+        sabs = Fraction(limbs_to_int(part[4:]), 1 << 128)
+        assert abs(float(sabs) - ref.sum_abs) <= 1e-12 * ref.sum_abs, c
+        assert abs(float(got - Fraction(ref.hi) - Fraction(ref.lo))) <= 4 * k * u * ref.sum_abs, c
+
+
 def test_launch_shape_does_not_change_bits(ctx):
     st, pat, O = gi.workload_m16_k10()
     O = gi.select(st.O, gi.random_pattern(16, 15, 3))
