@@ -228,7 +228,7 @@ def run_adaptive(args):
     rng = np.random.default_rng(3)
     # walked modes per chunk: at k >= 40 a chunk's root eliminates 26+ modes, so
     # longer chunks than the k <= 32 defaults keep the root a few percent of the walk
-    r1_of = {"fp64": 16, "dd": 13, "fx128": 13}
+    r1_of = {"fp64": 16, "dd": 13, "fx128": 13, "fx256": 13}
     window = 1 << 18                      # chunks per timed launch: 3.4 per thread of the grid
     out = {"metric": "adaptive precision: routed tier and projected single-GPU runtime (k=40, k=50)",
            "unit": "subset-dets/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
@@ -239,7 +239,7 @@ def run_adaptive(args):
         for k in (40, 50):
             Od = torch.from_numpy(gi.select(st.O, pat[:k])).cuda()
             bd = ctx.bounds([Od], tol=tol)[0]
-            routed = {1: "fp64", 2: "dd", 3: "fx128"}[int(bd["tier"])]
+            routed = {1: "fp64", 2: "dd", 3: "fx128", 4: "fx256"}[int(bd["tier"])]
             rows = {}
             for prec in dict.fromkeys([routed, "fp64"]):
                 d = k - r1_of[prec]

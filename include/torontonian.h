@@ -62,15 +62,20 @@ enum {
     TOR_ENOMEM = 6      /* workspace allocation failed */
 };
 
-enum { TOR_PREC_AUTO = 0, TOR_PREC_FP64 = 1, TOR_PREC_DD = 2, TOR_PREC_FX128 = 3 };
+enum { TOR_PREC_AUTO = 0, TOR_PREC_FP64 = 1, TOR_PREC_DD = 2, TOR_PREC_FX128 = 3, TOR_PREC_FX256 = 4 };
 /* TOR_PREC_FX128: the paper's 128-bit fixed point with one scaling factor
  * (Sec. 5.1-5.2), 104 fraction bits, on the integer pipe.  Every intermediate
  * must stay below 2^23 in magnitude; the largest are the pivot inverses
  * 1/det2 <= t_max^2 with t_max = 1/sqrt(det(I - O)), so tor_single requires
  * t_max <= 2^11 (checked by the bound pass, TOR_EINVAL otherwise); a product
  * that still leaves the range sets the result's status to TOR_EINVAL.
- * Available in tor_single, tor_single_async and tor_chunks (the latter two
- * do not run the range check). */
+ * Available in tor_single, tor_single_async, tor_chunks and tor_batch (the
+ * asynchronous single and chunk calls do not run the range check).
+ * TOR_PREC_FX256: the paper's 256-bit mode, 192 fraction bits; intermediates
+ * below 2^63, so t_max <= 2^30 is required.  Its terms carry 192 fraction
+ * bits, so its exact partial sums are 384-bit: tor_chunks writes 12 limbs per
+ * chunk for it (two 6-limb values with 192 fraction bits) instead of 8.
+ * Available in tor_single, tor_single_async and tor_chunks; batches refuse it. */
 enum { TOR_LAYOUT_XXPP = 0, TOR_LAYOUT_XPXP = 1 };
 
 typedef struct tor_ctx tor_ctx;
@@ -80,7 +85,7 @@ typedef struct {
     double hi, lo;      /* Tor = hi + lo */
     double sum_abs;     /* sum_Z t_Z (>= |Tor|) */
     double err_est;     /* a-posteriori bound on |computed - exact| */
-    int tier;           /* TOR_PREC_FP64, TOR_PREC_DD or TOR_PREC_FX128: arithmetic used */
+    int tier;           /* TOR_PREC_FP64, _DD, _FX128 or _FX256: arithmetic used */
     int status;         /* TOR_OK or TOR_ENOTPD for this instance */
 } tor_result;
 
@@ -90,7 +95,7 @@ typedef struct {
     float log_tor_est;    /* ln of the product estimate prod_j (tau_j - 1) of Tor */
     float log_kappa_est;  /* ln of the estimated condition number sum t / |Tor| */
     float bits_needed;    /* log2 kappa_est + log2(gamma) + log2(1/tol) */
-    int tier;             /* TOR_PREC_FP64 or TOR_PREC_DD */
+    int tier;             /* routed tier: TOR_PREC_FP64, _FX128, _FX256 or _DD (see tor_bounds) */
 } tor_bound;
 
 /* ------------------------------------------------------------------ context */
@@ -118,13 +123,17 @@ int tor_set_chunk_bits(tor_ctx *ctx, int chunk_bits);
 /*
  * tor_single: Tor of one 2k x 2k matrix (Eq. 2).
  *   O     dev  2k x 2k FP64, leading dimension ld, in `layout` order.
- *   prec  TOR_PREC_FP64, TOR_PREC_DD, TOR_PREC_FX128, or TOR_PREC_AUTO: the
- *         FP32 bound pass of tor_bounds picks the starting tier for relative
- *         tolerance `tol`; while the result's a-posteriori bound err_est
- *         exceeds tol * |Tor| it is recomputed one tier up (FP64 -> FX128
- *         when t_max <= 2^11, else double-double; FX128 -> double-double),
- *         and if double-double still misses, the call returns TOR_EPREC with
- *         the result filled in.  `tol` is ignored for the explicit tiers.
+ *   prec  TOR_PREC_FP64, TOR_PREC_DD, TOR_PREC_FX128, TOR_PREC_FX256, or
+ *         TOR_PREC_AUTO: the FP32 bound pass of tor_bounds picks the starting
+ *         tier for relative tolerance `tol`; while the result's a-posteriori
+ *         bound err_est exceeds tol * |Tor| it is recomputed in the next tier
+ *         with more precision that fits the instance's range (FP64 -> FX128
+ *         when t_max <= 2^11, else FX256 when t_max <= 2^30, else
+ *         double-double; FX128 -> FX256 or double-double; double-double ->
+ *         FX256), and when none is left the call returns TOR_EPREC with the
+ *         result filled in.  `tol` is ignored for the explicit tiers; the
+ *         fixed-point tiers return TOR_EINVAL for instances outside their
+ *         range.
  *   out   host result; the call synchronises `stream`.
  * The 2^k subsets are split into equal prefix chunks (the high modes of the
  * subset mask fixed per chunk, Algorithm 1's balanced partition) walked
@@ -152,7 +161,9 @@ int tor_single_async(tor_ctx *ctx, const double *O, int k, int ld, int layout, i
  *   part_dev    dev, (c_end - c_begin) x 8 uint64: per chunk the exact sum of
  *               (-1)^(k-|Z|) t_Z and of t_Z, each a 256-bit two's-complement
  *               fixed-point number with 128 fractional bits, little-endian
- *               64-bit limbs (limbs 0..3 = signed sum, 4..7 = sum_abs).
+ *               64-bit limbs (limbs 0..3 = signed sum, 4..7 = sum_abs).  For
+ *               TOR_PREC_FX256: x 12 uint64, two 384-bit values with 192
+ *               fractional bits (limbs 0..5 and 6..11).
  *   Partials of disjoint ranges add exactly (integer addition), so any split
  *   gives the same total bit for bit.
  */
@@ -179,9 +190,22 @@ int tor_chunks(tor_ctx *ctx, const double *O, int k, int ld, int layout, int pre
 int tor_single_noalloc(const double *O, int k, int ld, int layout, int prec,
                        cudaStream_t stream, tor_result *out_dev);
 
-/* Convert one 256-bit fixed-point pair (8 limbs as written by tor_chunks,
- * possibly summed over shards) to a tor_result (host, no GPU needed). */
-int tor_fixed_to_result(const uint64_t *limbs8, int k, int tier, tor_result *out);
+/* tor_fx256_mul: n elementwise products of 256-bit fixed-point numbers exactly
+ * as the TOR_PREC_FX256 tier forms them (Sec. 5.1-5.3: magnitudes multiplied,
+ * truncated to 192 fraction bits, sign restored), so that the arithmetic can
+ * be checked against an independent big-integer evaluation.
+ *   a_dev, b_dev  dev, n x 4 uint64: two's-complement values / 2^192,
+ *                 little-endian limbs.
+ *   out_dev       dev, n x 4 uint64 products.   ovf_dev  dev, n ints: 1 where
+ *                 the product's magnitude does not fit in 255 bits.
+ * Asynchronous on `stream`.  TOR_EINVAL for n < 0 or null pointers. */
+int tor_fx256_mul(const uint64_t *a_dev, const uint64_t *b_dev, int n, uint64_t *out_dev, int *ovf_dev,
+                  cudaStream_t stream);
+
+/* Convert one fixed-point pair as written by tor_chunks (8 limbs, or 12 for
+ * TOR_PREC_FX256), possibly summed over shards, to a tor_result (host, no
+ * GPU needed). */
+int tor_fixed_to_result(const uint64_t *limbs, int k, int tier, tor_result *out);
 
 /*
  * tor_batch: Tor of n matrices of different k (e.g. the patterns a sampler
@@ -240,8 +264,10 @@ int tor_batch_reserve(tor_ctx *ctx, int n_max, int k_max);
  * for the estimate's pessimism; AUTO callers verify the result's
  * a-posteriori bound and escalate), else TOR_PREC_FX128 if t_max <= 2^11 and
  * bits_needed <= 120 (the fixed-point unit's 100 bits plus the same slack),
- * else TOR_PREC_DD.  B not positive definite in FP32 gives bits_needed = +inf
- * and tier TOR_PREC_DD.  An instance with k
+ * else TOR_PREC_DD if bits_needed <= 124, else TOR_PREC_FX256 if
+ * t_max <= 2^30, else TOR_PREC_DD (batches, which have no 256-bit tier, run
+ * TOR_PREC_FX256 routes in double-double).  B not positive definite in FP32
+ * gives bits_needed = +inf and tier TOR_PREC_DD.  An instance with k
  * outside [0, TOR_MAX_K] or a null matrix gets tier 0 and NaN fields.
  * The estimates are heuristic: on Haar-mixed lossy GBS states kappa_est
  * over-estimates the true condition number by 10^2 to 10^13.

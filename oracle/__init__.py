@@ -10,6 +10,7 @@ Functions
 ---------
 tor(O)            Tor(O) of a 2k x 2k xxpp matrix; returns an OracleResult.
 tor_range(O, lo, hi)   the same sum restricted to subset masks in [lo, hi).
+tor_exact(O, lo, hi)   the same sums exactly, as Fractions (every bit of the fixed point).
 det(O, mask)      det(I - O_Z) for one subset mask (hi, lo).
 prob(Ofull, pattern)   click probability of Eq. 1 (hi, lo) plus Tor(O_S).
 fx_ops(a, b)      a*b, a+b, a-b, 1/a, 1/sqrt(a) through the fixed-point path.
@@ -64,8 +65,11 @@ def _load():
                                         ctypes.POINTER(ctypes.c_ubyte), ctypes.c_int, ctypes.c_int,
                                         dp]
             lib.oracle_fx_ops.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]
+            lib.oracle_tor_range_raw.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                                 ctypes.POINTER(ctypes.c_uint64)]
             for f in (lib.oracle_tor, lib.oracle_tor_range, lib.oracle_det, lib.oracle_prob,
-                      lib.oracle_fx_ops):
+                      lib.oracle_fx_ops, lib.oracle_tor_range_raw):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -116,6 +120,25 @@ def tor_range(O: np.ndarray, mask_lo: int, mask_hi: int, frac_bits: int = DEFAUL
     _check(_load().oracle_tor_range(_ptr(O), k, max(2 * k, 1), frac_bits, threads, mutation,
                                     mask_lo, mask_hi, _ptr(out)))
     return OracleResult(*map(float, out))
+
+
+def tor_exact(O: np.ndarray, mask_lo: int = 0, mask_hi: int | None = None,
+              frac_bits: int = DEFAULT_FRAC_BITS, threads: int = 0):
+    """(Tor, sum_Z t_Z) over the masks in [mask_lo, mask_hi) as exact Fractions of the
+    fixed-point sums (frac_bits fraction bits), not rounded to double-double."""
+    from fractions import Fraction
+    O = _as_c(O)
+    k = O.shape[0] // 2
+    if mask_hi is None:
+        mask_hi = 1 << k
+    raw = (ctypes.c_uint64 * 8)()
+    _check(_load().oracle_tor_range_raw(_ptr(O), k, max(2 * k, 1), frac_bits, threads, mask_lo,
+                                        mask_hi, raw))
+
+    def signed(words):
+        v = sum(int(w) << (64 * i) for i, w in enumerate(words))
+        return v - (1 << 256) if v >> 255 else v
+    return (Fraction(signed(raw[0:4]), 1 << frac_bits), Fraction(signed(raw[4:8]), 1 << frac_bits))
 
 
 def tor(O: np.ndarray, frac_bits: int = DEFAULT_FRAC_BITS, threads: int = 0,

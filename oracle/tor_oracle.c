@@ -239,8 +239,8 @@ static int det_I_minus_OZ(const double *O, int k, int ld, const int *idx, int m,
  *   summed (pass 0 and 2^k for the whole sum).
  * Returns ORC_OK or an ORC_* error.
  */
-int oracle_tor_range(const double *O, int k, int ld, int F, int nthreads, int mutation,
-                     uint64_t mask_lo, uint64_t mask_hi, double *out) {
+static int tor_range_fx(const double *O, int k, int ld, int F, int nthreads, int mutation,
+                        uint64_t mask_lo, uint64_t mask_hi, fx *tor_out, fx *sabs_out) {
     if (k < 0 || k > 40 || ld < 2 * k || F < 64 || F > 240) return ORC_EINVAL;
     uint64_t nmask = 1ull << k;
     if (mask_hi > nmask) mask_hi = nmask;
@@ -287,10 +287,36 @@ int oracle_tor_range(const double *O, int k, int ld, int F, int nthreads, int mu
             if (e2 && !status) status = e2;
         }
     }
+    *tor_out = tor;
+    *sabs_out = sabs;
+    return status;
+}
+
+int oracle_tor_range(const double *O, int k, int ld, int F, int nthreads, int mutation,
+                     uint64_t mask_lo, uint64_t mask_hi, double *out) {
+    fx tor, sabs;
+    int status = tor_range_fx(O, k, ld, F, nthreads, mutation, mask_lo, mask_hi, &tor, &sabs);
     fx_to_dd(tor, F, &out[0], &out[1]);
     fx_to_dd(sabs, F, &out[2], &out[3]);
     return status;
 }
+
+/*
+ * The same sum as oracle_tor_range, returned exactly: raw[0..3] = the signed
+ * sum, raw[4..7] = sum_Z t_Z, each a two's-complement 256-bit integer with F
+ * fractional bits (value = integer / 2^F), little-endian 64-bit limbs.  The
+ * double-double output of oracle_tor_range resolves only about 106 bits of
+ * the result; this one gives every bit the fixed-point arithmetic computed.
+ */
+int oracle_tor_range_raw(const double *O, int k, int ld, int F, int nthreads, uint64_t mask_lo,
+                         uint64_t mask_hi, uint64_t *raw) {
+    fx tor, sabs;
+    int status = tor_range_fx(O, k, ld, F, nthreads, 0, mask_lo, mask_hi, &tor, &sabs);
+    for (int i = 0; i < 4; ++i) { raw[i] = tor.w[i]; raw[4 + i] = sabs.w[i]; }
+    return status;
+}
+
+
 
 int oracle_tor(const double *O, int k, int ld, int F, int nthreads, int mutation, double *out) {
     if (k < 0 || k > 40) return ORC_EINVAL;

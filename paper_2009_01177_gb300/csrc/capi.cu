@@ -60,10 +60,10 @@ struct tor_ctx {
   unsigned char *r1_table_dev = nullptr;
   int *k_dev = nullptr;  // pattern mode: click counts
   Buf mh;                // sampler: proposals, their log q, their Torontonians
-  unsigned char r1_table[4][65];  // walked modes per chunk, by tier (TOR_PREC_*) and k
+  unsigned char r1_table[5][65];  // walked modes per chunk, by tier (TOR_PREC_*) and k
   // autotuned single-instance settings by tier and k (-1: not tuned)
-  signed char tuned_d[4][65];   // by tier (TOR_PREC_FP64 .. TOR_PREC_FX128) and k
-  signed char tuned_bps[4][65];
+  signed char tuned_d[5][65];   // by tier (TOR_PREC_FP64 .. TOR_PREC_FX256) and k
+  signed char tuned_bps[5][65];
 };
 
 namespace {
@@ -90,9 +90,14 @@ int ensure(tor_ctx *c, Buf &b, size_t bytes) {
 int choose_chunk_bits(const tor_ctx *c, int k, int tier = TOR_PREC_FP64) {
   if (c->chunk_bits >= 0) return c->chunk_bits < k ? c->chunk_bits : k;
   if (k <= 64 && c->tuned_d[tier][k] >= 0) return c->tuned_d[tier][k];
-  int d = k - 10;
-  const int cap = (k >= 36) ? 20 : 18;
-  if (d > cap) d = cap;
+  // 2^16 chunks fill a 152-SM grid (about 58k threads) with one to two rounds;
+  // beyond k = 32 the chunks stay at 16 walked modes, where a chunk's root (the
+  // elimination of its fixed modes) costs a few percent of its walk.  The
+  // autotuner's choices at k = 28, 30, 32 on GB300 are d = 15, 16, 16.
+  int d = k - 16;
+  const int fill = (k - 8 < 16) ? k - 8 : 16;
+  if (d < fill) d = fill;
+  if (d > 40) d = 40;
   if (d < 0) d = 0;
   return d;
 }
@@ -162,7 +167,7 @@ int enqueue_walk(tor_ctx *ctx, const double *O, int k, int ld, int layout, int t
   if ((rc = ensure(ctx, ctx->B, sizeof(double) * 4 * (size_t)k * k))) return rc;
   if ((rc = ensure(ctx, ctx->Blo, sizeof(double) * 2 * (size_t)k))) return rc;
   if ((rc = ensure(ctx, ctx->scratch, sizeof(double) * nthreads * (size_t)tor::scratch_entries(tier, k, r1)))) return rc;
-  if ((rc = ensure(ctx, ctx->block_part, sizeof(unsigned long long) * 8 * (size_t)grid))) return rc;
+  if ((rc = ensure(ctx, ctx->block_part, sizeof(unsigned long long) * 12 * (size_t)grid))) return rc;
   if ((rc = ensure(ctx, ctx->status, sizeof(int)))) return rc;
   tor::launch_prep(O, k, ld, layout, (double *)ctx->B.p, (double *)ctx->Blo.p, s);
   CK(cudaGetLastError());
@@ -207,6 +212,7 @@ int tor_create(tor_ctx **out, int device) {
     c->r1_table[TOR_PREC_FP64][kk] = (unsigned char)(kk < 14 ? kk : 14);
     c->r1_table[TOR_PREC_DD][kk] = (unsigned char)(kk < 12 ? kk : 12);
     c->r1_table[TOR_PREC_FX128][kk] = (unsigned char)(kk < 12 ? kk : 12);
+    c->r1_table[TOR_PREC_FX256][kk] = (unsigned char)(kk < 12 ? kk : 12);
   }
   cudaError_t e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess) {
@@ -274,8 +280,8 @@ int tor_single_async(tor_ctx *ctx, const double *O, int k, int ld, int layout, i
   int rc = check_common(ctx, O, k, ld, layout);
   if (rc) return rc;
   if (!out_dev) return fail(TOR_EINVAL, "null result pointer");
-  if (prec != TOR_PREC_FP64 && prec != TOR_PREC_DD && prec != TOR_PREC_FX128)
-    return fail(TOR_EINVAL, "tor_single_async needs TOR_PREC_FP64, TOR_PREC_DD or TOR_PREC_FX128");
+  if (prec < TOR_PREC_FP64 || prec > TOR_PREC_FX256)
+    return fail(TOR_EINVAL, "tor_single_async needs an explicit tier (TOR_PREC_FP64 .. TOR_PREC_FX256)");
   CK(cudaSetDevice(ctx->device));
   if (k == 0) {
     tor_result one = {1.0, 0.0, 1.0, 0.0, prec, TOR_OK};
@@ -292,7 +298,7 @@ int tor_single_async(tor_ctx *ctx, const double *O, int k, int ld, int layout, i
   rc = enqueue_walk(ctx, O, k, ld, layout, prec, seg, nullptr, s, grid);
   if (rc) return rc;
   tor::launch_finalize((const unsigned long long *)ctx->block_part.p, grid, k, prec,
-                       (const int *)ctx->status.p, out_dev, nullptr, s);
+                       (const int *)ctx->status.p, out_dev, s);
   CK(cudaGetLastError());
   return TOR_OK;
 }
@@ -313,10 +319,9 @@ int tor_single(tor_ctx *ctx, const double *O, int k, int ld, int layout, int pre
   int rc = check_common(ctx, O, k, ld, layout);
   if (rc) return rc;
   if (!out) return fail(TOR_EINVAL, "null result pointer");
-  if (prec != TOR_PREC_AUTO && prec != TOR_PREC_FP64 && prec != TOR_PREC_DD && prec != TOR_PREC_FX128)
-    return fail(TOR_EINVAL, "bad precision %d", prec);
+  if (prec < TOR_PREC_AUTO || prec > TOR_PREC_FX256) return fail(TOR_EINVAL, "bad precision %d", prec);
   int tier = prec;
-  if (prec == TOR_PREC_FX128 && k > 0) {  // the fixed-point range: 1/det2 <= t_max^2 must fit
+  if ((prec == TOR_PREC_FX128 || prec == TOR_PREC_FX256) && k > 0) {  // 1/det2 <= t_max^2 must fit
     CK(cudaSetDevice(ctx->device));
     if ((rc = ensure(ctx, ctx->bound, sizeof(tor_bound)))) return rc;
     if (tor::launch_bounds_single(O, k, ld, layout, 1e-10, (tor_bound *)ctx->bound.p, s))
@@ -324,11 +329,12 @@ int tor_single(tor_ctx *ctx, const double *O, int k, int ld, int layout, int pre
     tor_bound bd;
     CK(cudaMemcpyAsync(&bd, ctx->bound.p, sizeof(bd), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (!(bd.log_tmax <= tor::FX128_MAX_LOG2_TMAX * 0.6931472f))
-      return fail(TOR_EINVAL, "instance outside the 128-bit fixed-point range (log2 t_max = %.2f > %.0f)",
-                  (double)bd.log_tmax / 0.6931472, (double)tor::FX128_MAX_LOG2_TMAX);
+    const float lim = (prec == TOR_PREC_FX128) ? tor::FX128_MAX_LOG2_TMAX : tor::FX256_MAX_LOG2_TMAX;
+    if (!(bd.log_tmax <= lim * 0.6931472f))
+      return fail(TOR_EINVAL, "instance outside the %d-bit fixed-point range (log2 t_max = %.2f > %.0f)",
+                  prec == TOR_PREC_FX128 ? 128 : 256, (double)bd.log_tmax / 0.6931472, (double)lim);
   }
-  bool fx_ok = false;  // t_max inside the fixed-point range
+  bool fx_ok = false, fx4_ok = false;  // t_max inside the 128-bit / 256-bit fixed-point range
   if (prec == TOR_PREC_AUTO) {
     if (!(tol > 0.0)) return fail(TOR_EINVAL, "TOR_PREC_AUTO needs a tolerance tol > 0");
     tier = TOR_PREC_FP64;
@@ -342,6 +348,7 @@ int tor_single(tor_ctx *ctx, const double *O, int k, int ld, int layout, int pre
       CK(cudaStreamSynchronize(s));
       tier = bd.tier;
       fx_ok = bd.log_tmax <= tor::FX128_MAX_LOG2_TMAX * 0.6931472f;
+      fx4_ok = bd.log_tmax <= tor::FX256_MAX_LOG2_TMAX * 0.6931472f;
     }
   }
   while (true) {
@@ -352,11 +359,18 @@ int tor_single(tor_ctx *ctx, const double *O, int k, int ld, int layout, int pre
     if (prec != TOR_PREC_AUTO) return TOR_OK;
     const double mag = out->hi < 0 ? -out->hi : out->hi;
     if (out->err_est <= tol * mag) return TOR_OK;
-    if (tier == TOR_PREC_DD)
-      return fail(TOR_EPREC, "error bound %.3e exceeds tol * |Tor| = %.3e even in double-double",
+    // a-posteriori escalation to the next tier with more precision that fits:
+    // FP64 (53 bits) -> 128-bit fixed point (100) or double-double (104) ->
+    // 256-bit fixed point (186); double-double adds only 4 bits to the 128-bit
+    // fixed point, so that step goes straight to 256 bits when it can
+    int next = 0;
+    if (tier == TOR_PREC_FP64) next = fx_ok ? TOR_PREC_FX128 : (fx4_ok ? TOR_PREC_FX256 : TOR_PREC_DD);
+    else if (tier == TOR_PREC_FX128) next = fx4_ok ? TOR_PREC_FX256 : TOR_PREC_DD;
+    else if (tier == TOR_PREC_DD) next = fx4_ok ? TOR_PREC_FX256 : 0;
+    if (next == 0)
+      return fail(TOR_EPREC, "error bound %.3e exceeds tol * |Tor| = %.3e in the most precise tier that fits",
                   out->err_est, tol * mag);
-    // a-posteriori escalation, one tier up
-    tier = (tier == TOR_PREC_FP64 && fx_ok) ? TOR_PREC_FX128 : TOR_PREC_DD;
+    tier = next;
   }
 }
 
@@ -365,8 +379,7 @@ int tor_chunks(tor_ctx *ctx, const double *O, int k, int ld, int layout, int pre
   int rc = check_common(ctx, O, k, ld, layout);
   if (rc) return rc;
   if (k == 0) return fail(TOR_EINVAL, "tor_chunks needs k >= 1");
-  if (prec != TOR_PREC_FP64 && prec != TOR_PREC_DD && prec != TOR_PREC_FX128)
-    return fail(TOR_EINVAL, "prec must be FP64, DD or FX128");
+  if (prec < TOR_PREC_FP64 || prec > TOR_PREC_FX256) return fail(TOR_EINVAL, "prec must be an explicit tier");
   if (chunk_bits < 0 || chunk_bits > k || chunk_bits > 40) return fail(TOR_EINVAL, "chunk_bits outside [0, min(k, 40)]");
   if (!part_dev) return fail(TOR_EINVAL, "null partials pointer");
   const uint64_t nchunks = 1ull << chunk_bits;
@@ -379,10 +392,20 @@ int tor_chunks(tor_ctx *ctx, const double *O, int k, int ld, int layout, int pre
                       (unsigned long long *)part_dev, s, walk_grid(ctx, prec));
 }
 
-int tor_fixed_to_result(const uint64_t *limbs8, int k, int tier, tor_result *out) {
-  if (!limbs8 || !out) return fail(TOR_EINVAL, "null pointer");
-  if (tier != TOR_PREC_FP64 && tier != TOR_PREC_DD && tier != TOR_PREC_FX128) return fail(TOR_EINVAL, "bad tier");
-  tor::fixed_to_result((const unsigned long long *)limbs8, k, tier, 0, out);
+int tor_fx256_mul(const uint64_t *a_dev, const uint64_t *b_dev, int n, uint64_t *out_dev, int *ovf_dev,
+                  cudaStream_t stream) {
+  if (n < 0) return fail(TOR_EINVAL, "n = %d < 0", n);
+  if (n > 0 && (!a_dev || !b_dev || !out_dev || !ovf_dev)) return fail(TOR_EINVAL, "null pointer");
+  if (tor::launch_fx256_mul((const unsigned long long *)a_dev, (const unsigned long long *)b_dev, n,
+                            (unsigned long long *)out_dev, ovf_dev, stream))
+    return fail(TOR_ECUDA, "launch: %s", cudaGetErrorString(cudaGetLastError()));
+  return TOR_OK;
+}
+
+int tor_fixed_to_result(const uint64_t *limbs, int k, int tier, tor_result *out) {
+  if (!limbs || !out) return fail(TOR_EINVAL, "null pointer");
+  if (tier < TOR_PREC_FP64 || tier > TOR_PREC_FX256) return fail(TOR_EINVAL, "bad tier");
+  tor::fixed_to_result((const unsigned long long *)limbs, k, tier, 0, out);
   return TOR_OK;
 }
 
@@ -409,7 +432,7 @@ static int batch_reserve(tor_ctx *ctx, int n_max, int k_max) {
   const size_t sz_tier = al(n), sz_r1 = al(n), sz_esc = al(n), sz_key = al(4 * n), sz_order = al(4 * n),
                sz_flags = al(4 * n), sz_off = al(8 * (n + 1)), sz_acc = al(64 * n), sz_range = al(48),
                sz_counter = al(24), sz_counts = al(12), sz_result = al(sizeof(tor_result) * n),
-               sz_bounds = al(sizeof(tor_bound) * n), sz_r1tab = al(4 * 65), sz_k = al(4 * n);
+               sz_bounds = al(sizeof(tor_bound) * n), sz_r1tab = al(5 * 65), sz_k = al(4 * n);
   const size_t total = sz_tier + sz_r1 + sz_esc + sz_key + sz_order + sz_flags + sz_off + sz_acc + sz_range +
                        sz_counter + sz_counts + sz_result + sz_bounds + sz_r1tab + sz_k;
   int rc;
@@ -509,6 +532,7 @@ static int batch_autoreserve(tor_ctx *ctx, const int *k_dev, int n, cudaStream_t
 static int batch_check(tor_ctx *ctx, int n, int prec, double tol) {
   if (!ctx) return fail(TOR_EINVAL, "null context");
   if (n < 0) return fail(TOR_EINVAL, "n = %d < 0", n);
+  if (prec == TOR_PREC_FX256) return fail(TOR_EINVAL, "batches run FP64, DD, FX128 or AUTO; FX256 is single-instance");
   if (prec != TOR_PREC_AUTO && prec != TOR_PREC_FP64 && prec != TOR_PREC_DD && prec != TOR_PREC_FX128)
     return fail(TOR_EINVAL, "bad precision %d", prec);
   if (prec == TOR_PREC_AUTO && !(tol > 0.0)) return fail(TOR_EINVAL, "TOR_PREC_AUTO needs tol > 0");
@@ -635,7 +659,7 @@ bool parse_line(const char *line, TuneEntry &e) {
   e.d = atoi(d + 14);
   e.bps = atoi(b + 17);
   e.ms = atof(m + 6);
-  return e.k >= 0 && e.k <= 64 && e.tier >= TOR_PREC_FP64 && e.tier <= TOR_PREC_FX128 && e.d >= 0 && e.d <= e.k &&
+  return e.k >= 0 && e.k <= 64 && e.tier >= TOR_PREC_FP64 && e.tier <= TOR_PREC_FX256 && e.d >= 0 && e.d <= e.k &&
          e.bps >= 1 && e.bps <= 16;
 }
 
@@ -645,8 +669,7 @@ int tor_autotune(tor_ctx *ctx, int k, int prec, const char *cache_path, int *chu
                  int *blocks_per_sm_out) {
   if (!ctx) return fail(TOR_EINVAL, "null context");
   if (k < 1 || k > 40) return fail(TOR_EINVAL, "autotune k = %d outside [1, 40]", k);
-  if (prec != TOR_PREC_FP64 && prec != TOR_PREC_DD && prec != TOR_PREC_FX128)
-    return fail(TOR_EINVAL, "prec must be FP64, DD or FX128");
+  if (prec < TOR_PREC_FP64 || prec > TOR_PREC_FX256) return fail(TOR_EINVAL, "prec must be an explicit tier");
   CK(cudaSetDevice(ctx->device));
   cudaDeviceProp prop;
   CK(cudaGetDeviceProperties(&prop, ctx->device));

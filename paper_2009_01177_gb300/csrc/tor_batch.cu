@@ -76,6 +76,7 @@ k_batch_plan(const int *__restrict__ k, const tor_bound *__restrict__ bounds, in
     int tier;
     if (mode == 0) {
       tier = (prec == TOR_PREC_AUTO) ? (bounds ? bounds[i].tier : TOR_PREC_FP64) : prec;
+      if (tier == TOR_PREC_FX256) tier = TOR_PREC_DD;  // batches have no 256-bit tier
       if (ki < 0 || ki > kmax) tier = 0;
       if (tier == TOR_PREC_FX128 && ki > 0 && !(bounds && fx_in_range(bounds[i]))) tier = 0;
       p.tier[i] = (unsigned char)tier;

@@ -26,8 +26,10 @@
 // So the routing is optimistic: tier = FP64 if bits_needed <= 52 + 20 (the
 // estimate may overshoot by 2^20); else the 128-bit fixed-point tier if the
 // instance fits its range (t_max <= 2^11) and bits_needed <= 100 + 20; else
-// double-double.  Fixed point runs about 3x faster than double-double at a
-// 16x looser error bound (u = 2^-100 against 2^-104).
+// double-double if bits_needed <= 104 + 20; else the 256-bit fixed-point tier
+// if it fits (t_max <= 2^30); else double-double (the result then carries a
+// bound above the tolerance).  The 128-bit fixed point runs about 3x faster
+// than double-double at a 16x looser error bound (u = 2^-100 against 2^-104).
 //
 // One block of 64 threads per instance; B is held in FP32 in shared memory.
 #include <cuda_runtime.h>
@@ -40,6 +42,7 @@ namespace tor {
 constexpr int BOUNDS_THREADS = 64;
 constexpr float FP64_ROUTE_BITS = 52.f + 20.f;   // optimistic FP64 attempt, see above
 constexpr float FX128_ROUTE_BITS = 100.f + 20.f; // the same slack over the fixed-point unit
+constexpr float DD_ROUTE_BITS = 104.f + 20.f;
 
 // O entries of one instance in mode-interleaved local coordinates (row = 2m + q)
 struct OInstance {
@@ -119,8 +122,11 @@ __device__ void bounds_one(const Get &getO, bool valid, int k, double tol, float
                        (float)log2(1.0 / (tol > 0 ? tol : 1e-300));
     bd.bits_needed = s_bad ? INFINITY : bits;
     const bool fx_ok = !s_bad && bd.log_tmax <= FX128_MAX_LOG2_TMAX * 0.6931472f;
+    const bool fx4_ok = !s_bad && bd.log_tmax <= FX256_MAX_LOG2_TMAX * 0.6931472f;
     bd.tier = (!s_bad && bits <= FP64_ROUTE_BITS)            ? TOR_PREC_FP64
               : (fx_ok && bits <= FX128_ROUTE_BITS)           ? TOR_PREC_FX128
+              : (!s_bad && bits <= DD_ROUTE_BITS)             ? TOR_PREC_DD
+              : fx4_ok                                        ? TOR_PREC_FX256
                                                               : TOR_PREC_DD;
     *out = bd;
   }

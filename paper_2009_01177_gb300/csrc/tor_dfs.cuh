@@ -47,6 +47,7 @@
 #include "fixacc.cuh"
 #include "dd.cuh"
 #include "fx128.cuh"
+#include "fx256.cuh"
 
 namespace tor {
 
@@ -57,11 +58,13 @@ __host__ __device__ constexpr int ix(int hi, int lo) { return hi * (hi + 1) / 2 
 enum : int { ST_NOTPD = 1, ST_RANGE = 2 };  // ST_RANGE also marks fixed-point overflow
 
 // ----------------------------------------------------------- accumulators
-struct Sums {
-  Fx256 tor;   // sum of (-1)^(k-|Z|) t_Z
-  Fx256 sabs;  // sum of t_Z
+template <class A>
+struct SumsOf {
+  A tor;   // sum of (-1)^(k-|Z|) t_Z
+  A sabs;  // sum of t_Z
   int flags;
 };
+using Sums = SumsOf<Fx256>;
 
 // acc += (neg ? -|x| : |x|); tiny magnitudes (< 2^-75) are dropped (their
 // contribution is far below any result's resolution); x must be finite.
@@ -118,6 +121,17 @@ __device__ __forceinline__ void fx_add_signed(Fx256 &acc, double x, bool neg, in
 #endif
 #ifndef TOR_FX_MINB
 #define TOR_FX_MINB 4
+#endif
+// The 256-bit tier: values are eight registers, so one-mode register subtrees
+// and small shared-memory nodes (four doubles per entry).
+#ifndef TOR_FX4_RREG
+#define TOR_FX4_RREG 1
+#endif
+#ifndef TOR_FX4_RSMEM
+#define TOR_FX4_RSMEM 2
+#endif
+#ifndef TOR_FX4_MINB
+#define TOR_FX4_MINB 2
 #endif
 
 __device__ __forceinline__ double dmul(double a, double b) { return a * b; }
@@ -189,6 +203,7 @@ struct TierF64 {
   static constexpr int RSMEM = TOR_F64_RSMEM;     // shared-memory node size (modes), <= RREG + 2
   static constexpr int MINB = TOR_F64_MINB;       // __launch_bounds__ minimum blocks per SM
   static constexpr int PREC = 1;                  // TOR_PREC_FP64
+  using Acc = Fx256;                              // exact accumulator of the terms
 
   __device__ static __forceinline__ T ld(const double *P, int e, size_t st) { return P[(size_t)e * st]; }
   __device__ static __forceinline__ void stv(double *P, int e, size_t st, T v) { P[(size_t)e * st] = v; }
@@ -232,6 +247,7 @@ struct TierDD {
   static constexpr int RSMEM = TOR_DD_RSMEM;
   static constexpr int MINB = 1;
   static constexpr int PREC = 2;  // TOR_PREC_DD
+  using Acc = Fx256;
 
   __device__ static __forceinline__ T ld(const double *P, int e, size_t st) {
     return {P[(size_t)(2 * e) * st], P[(size_t)(2 * e + 1) * st]};
@@ -281,6 +297,7 @@ struct TierFx {
   static constexpr int RSMEM = TOR_FX_RSMEM;
   static constexpr int MINB = TOR_FX_MINB;
   static constexpr int PREC = 3;  // TOR_PREC_FX128
+  using Acc = Fx256;
   static constexpr int FRAC = F;
   static_assert(F >= 64 && F <= 124, "fraction bits");
 
@@ -377,6 +394,116 @@ struct TierFx {
   }
 };
 
+// ------------------------------------------------- 256-bit fixed-point tier
+// The paper's 256-bit mode (Sec. 5.1-5.2): 256-bit two's-complement integers
+// with 192 fraction bits (fx256.cuh), four doubles per stored entry.  Every
+// intermediate must stay below 2^63; the largest are the pivot inverses
+// 1/det2 <= t_max^2, so instances need t_max <= 2^30.  The terms carry 192
+// fraction bits, so they go to 384-bit accumulators (192 fraction bits).
+struct TierFx4 {
+  using T = fx4;
+  using Acc = Fx384;
+  static constexpr int W = 4;
+  static constexpr int RREG = TOR_FX4_RREG;
+  static constexpr int RUNROLL = 0;
+  static constexpr int RSMEM = TOR_FX4_RSMEM;
+  static constexpr int MINB = TOR_FX4_MINB;
+  static constexpr int PREC = 4;  // TOR_PREC_FX256
+
+  __device__ static __forceinline__ T ld(const double *P, int e, size_t st) {
+    T v;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v.w[i] = (unsigned long long)__double_as_longlong(P[(size_t)(4 * e + i) * st]);
+    return v;
+  }
+  __device__ static __forceinline__ void stv(double *P, int e, size_t st, T v) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) P[(size_t)(4 * e + i) * st] = __longlong_as_double((long long)v.w[i]);
+  }
+  __device__ static __forceinline__ T one() { return {{0ull, 0ull, 0ull, 1ull}}; }
+  // exact for 2^-139 <= |x| < 2^10 (53 mantissa bits at or above 2^-192);
+  // smaller magnitudes lose their low bits, larger ones set ST_RANGE
+  __device__ static __forceinline__ T from_double(double x, int &fl) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7FF);
+    T r = {{0ull, 0ull, 0ull, 0ull}};
+    if (e == 0) return r;
+    const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    const int sh = e - 1075 + FX256_FRAC;  // value = m 2^sh in units of 2^-192
+    if (sh < 0) {
+      r.w[0] = (sh > -64) ? (m >> (-sh)) : 0ull;
+    } else if (sh + 53 > 255) {
+      fl |= ST_RANGE;
+    } else {
+      const int q = sh >> 6, sb = sh & 63;
+      const unsigned long long lo = m << sb, hi = sb ? (m >> (64 - sb)) : 0ull;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) r.w[i] = (q == i) ? lo : ((q + 1 == i) ? hi : 0ull);
+    }
+    return (bits >> 63) ? fx4_neg(r) : r;
+  }
+  __device__ static __forceinline__ double to_double(const T &x) {
+    const bool neg = fx4_neg_p(x);
+    const T m = neg ? fx4_neg(x) : x;
+    const double d = (double)m.w[3] + (double)m.w[2] * 0x1p-64 + (double)m.w[1] * 0x1p-128;
+    return neg ? -d : d;
+  }
+  __device__ static __forceinline__ T from_hilo(double h, double l) {
+    int fl = 0;
+    return fx4_add(from_double(h, fl), from_double(l, fl));
+  }
+  __device__ static __forceinline__ T from_o(double o, bool diag) {
+    int fl = 0;
+    const T v = from_double(o, fl);
+    return diag ? fx4_sub(one(), v) : fx4_neg(v);
+  }
+  __device__ static __forceinline__ T mul(T a, T b, int &fl) {
+    int o = 0;
+    const T r = fx4_mul(a, b, o);
+    if (o) fl |= ST_RANGE;
+    return r;
+  }
+  __device__ static __forceinline__ T det2(T a, T b, T d, int &fl) { return fx4_sub(mul(a, d, fl), mul(b, b, fl)); }
+  __device__ static __forceinline__ bool bad(T x) {
+    return fx4_neg_p(x) || ((x.w[0] | x.w[1] | x.w[2] | x.w[3]) == 0ull);
+  }
+  // 1/sqrt(x): an FP64 seed (about 52 bits) and two fixed-point Newton steps
+  // y <- y (3 - x y^2) / 2, which take it past the 192 fraction bits
+  __device__ static __forceinline__ T rsqrt(T x, int &fl) {
+    const double xd = to_double(x);
+    T y = from_double(xd > 0.0 ? rsqrt_fp64(xd) : 0.0, fl);
+    const T three = {{0ull, 0ull, 0ull, 3ull}};
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const T e = fx4_sub(three, mul(x, mul(y, y, fl), fl));
+      const T p = mul(y, e, fl);
+      y.w[0] = (p.w[0] >> 1) | (p.w[1] << 63);  // / 2 (arithmetic shift)
+      y.w[1] = (p.w[1] >> 1) | (p.w[2] << 63);
+      y.w[2] = (p.w[2] >> 1) | (p.w[3] << 63);
+      y.w[3] = (unsigned long long)((long long)p.w[3] >> 1);
+    }
+    return y;
+  }
+  __device__ static __forceinline__ void coef(T a, T b, T d, T y, T &al, T &be, T &de, int &fl) {
+    const T inv = mul(y, y, fl);
+    al = mul(d, inv, fl); be = mul(b, inv, fl); de = mul(a, inv, fl);
+  }
+  __device__ static __forceinline__ void vrow(T al, T be, T de, T ux, T up, T &vx, T &vp, int &fl) {
+    vx = fx4_sub(mul(al, ux, fl), mul(be, up, fl));
+    vp = fx4_sub(mul(de, up, fl), mul(be, ux, fl));
+  }
+  __device__ static __forceinline__ T upd(T s, T vx, T ux, T vp, T up, int &fl) {
+    return fx4_sub(fx4_sub(s, mul(vx, ux, fl)), mul(vp, up, fl));
+  }
+  // t (192 fraction bits, positive) into the 192-fraction-bit accumulators, exactly
+  __device__ static __forceinline__ void acc(SumsOf<Fx384> &S, T t, bool neg) {
+    if (fx4_neg_p(t)) { S.flags |= ST_RANGE; return; }
+    const Fx384 X = {{t.w[0], t.w[1], t.w[2], t.w[3], 0ull, 0ull}};
+    if (neg) fx_sub(S.tor, X); else fx_add(S.tor, X);
+    fx_add(S.sabs, X);
+  }
+};
+
 // ------------------------------------------------------ register subtrees
 template <class Tier, int R>
 struct RegNode;
@@ -385,7 +512,7 @@ struct RegNode;
 template <class Tier, int RP, class Get>
 __device__ __forceinline__ void reg_child(const Get &get, typename Tier::T a, typename Tier::T b,
                                           typename Tier::T d, typename Tier::T y,
-                                          typename Tier::T tc, int parc, int k, Sums &S) {
+                                          typename Tier::T tc, int parc, int k, SumsOf<typename Tier::Acc> &S) {
   using T = typename Tier::T;
   int &FL = S.flags;
   T al, be, de;
@@ -410,7 +537,7 @@ __device__ __forceinline__ void reg_child(const Get &get, typename Tier::T a, ty
 template <class Tier, int R, int RP>
 struct RegChildren {
   using T = typename Tier::T;
-  __device__ static __forceinline__ void run(const T (&M)[sz(R)], T t, int par, int k, Sums &S) {
+  __device__ static __forceinline__ void run(const T (&M)[sz(R)], T t, int par, int k, SumsOf<typename Tier::Acc> &S) {
     int &FL = S.flags;
     const T a = M[ix(2 * RP + 1, 2 * RP + 1)], b = M[ix(2 * RP + 1, 2 * RP)], d = M[ix(2 * RP, 2 * RP)];
     const T det2 = Tier::det2(a, b, d, FL);
@@ -428,13 +555,13 @@ struct RegChildren {
 template <class Tier, int R>
 struct RegChildren<Tier, R, R> {
   using T = typename Tier::T;
-  __device__ static __forceinline__ void run(const T (&)[sz(R)], T, int, int, Sums &) {}
+  __device__ static __forceinline__ void run(const T (&)[sz(R)], T, int, int, SumsOf<typename Tier::Acc> &) {}
 };
 
 template <class Tier, int R>
 struct RegNode {
   using T = typename Tier::T;
-  __device__ static __forceinline__ void visit(const T (&M)[sz(R)], T t, int par, int k, Sums &S) {
+  __device__ static __forceinline__ void visit(const T (&M)[sz(R)], T t, int par, int k, SumsOf<typename Tier::Acc> &S) {
     RegChildren<Tier, R, 0>::run(M, t, par, k, S);
   }
 };
@@ -444,7 +571,7 @@ template <class Tier>
 __device__ __forceinline__ void mem_to_reg_child(int rp, const double *P, size_t st,
                                                  typename Tier::T a, typename Tier::T b,
                                                  typename Tier::T d, typename Tier::T y,
-                                                 typename Tier::T tc, int parc, int k, Sums &S) {
+                                                 typename Tier::T tc, int parc, int k, SumsOf<typename Tier::Acc> &S) {
   auto get = [&](int e) { return Tier::ld(P, e, st); };
   if constexpr (Tier::RREG >= 1) { if (rp == 1) { reg_child<Tier, 1>(get, a, b, d, y, tc, parc, k, S); return; } }
   if constexpr (Tier::RREG >= 2) { if (rp == 2) { reg_child<Tier, 2>(get, a, b, d, y, tc, parc, k, S); return; } }
@@ -540,7 +667,7 @@ __host__ __device__ constexpr int stack_entries(int r, int rreg) {
 // Q/sq: this thread's shared-memory slot (Tier::RSMEM nodes; may be null to
 // keep every node in global memory).
 template <class Tier>
-__device__ void dfs_walk(double *S, size_t st, int r, typename Tier::T t, int par, int k, Sums &Sm,
+__device__ void dfs_walk(double *S, size_t st, int r, typename Tier::T t, int par, int k, SumsOf<typename Tier::Acc> &Sm,
                          double *Q = nullptr, size_t sq = 0) {
   using T = typename Tier::T;
   // a shared-memory node's only child above RREG is its last one, written in place
@@ -594,11 +721,12 @@ __device__ void dfs_walk(double *S, size_t st, int r, typename Tier::T t, int pa
 }
 
 // shared-memory bytes a walk kernel needs per block: the per-thread slots, and
-// at least the 64 bytes per thread of the block's partial-sum reduction
+// at least the two accumulators per thread of the block's partial-sum reduction
 template <class Tier>
 __host__ __device__ constexpr size_t walk_smem_bytes(int threads) {
   const size_t slot = (size_t)sz(Tier::RSMEM) * Tier::W * sizeof(double);
-  return (slot > 64 ? slot : 64) * (size_t)threads;
+  const size_t red = 2 * sizeof(typename Tier::Acc);
+  return (slot > red ? slot : red) * (size_t)threads;
 }
 
 }  // namespace tor

@@ -11,13 +11,19 @@ namespace tor {
 // error of the Schur updates; gamma = 4k covers those with margin.
 __host__ __device__ inline double err_gamma(int k) { return 4.0 * (k > 1 ? k : 1); }
 // fixed point: absolute rounding 2^-104 per product, relative 2^-100 for the
-// values >= 1/16 the walk carries (Schur entries, pivots, terms)
+// values >= 1/16 the walk carries (Schur entries, pivots, terms); 256-bit:
+// 2^-192 per product plus at most a few units of dropped carries, 2^-186
 __host__ __device__ inline double unit_roundoff(int tier) {
-  return tier == TOR_PREC_DD ? 0x1p-104 : (tier == TOR_PREC_FX128 ? 0x1p-100 : 0x1p-53);
+  return tier == TOR_PREC_DD      ? 0x1p-104
+         : tier == TOR_PREC_FX128 ? 0x1p-100
+         : tier == TOR_PREC_FX256 ? 0x1p-186
+                                  : 0x1p-53;
 }
 constexpr int FX128_FRAC = 104;
 // largest log2 t_max for which every intermediate fits: 2 log2 t_max < 127 - F - 1
 constexpr float FX128_MAX_LOG2_TMAX = 11.0f;
+// the same for the 256-bit tier: 2 log2 t_max < 255 - 192 - 1
+constexpr float FX256_MAX_LOG2_TMAX = 30.0f;
 
 // device arrays of a batch plan (sized for n_max instances by tor_batch_reserve)
 struct BatchPlan {
@@ -74,8 +80,10 @@ void launch_dfs(int tier, int grid, int block, const double *B, const double *Bl
                 double *scratch, unsigned long long *block_part, unsigned long long *chunk_part, int *status,
                 cudaStream_t s);
 void launch_finalize(const unsigned long long *block_part, int nblocks, int k, int tier,
-                     const int *status, tor_result *out, unsigned long long *total8, cudaStream_t s);
+                     const int *status, tor_result *out, cudaStream_t s);
 void launch_dfma_peak(double *sink, int grid, int block, int iters, cudaStream_t s);
+int launch_fx256_mul(const unsigned long long *a, const unsigned long long *b, int n, unsigned long long *out,
+                     int *ovf, cudaStream_t s);
 int scratch_entries(int tier, int k, int r1);
 int dfs_max_blocks_per_sm(int tier, int block);
 int launch_bounds_batch(const double *const *O, const int *k, const int *ld, int n, int layout, double tol,

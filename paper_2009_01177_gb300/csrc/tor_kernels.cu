@@ -48,7 +48,9 @@ k_dfs(const double *__restrict__ B, const double *__restrict__ Blo, int k, const
   double *Q = smem + threadIdx.x;  // this thread's shared-memory node slot (stride blockDim.x)
   const SrcPrepped src{B, Blo, 2 * k};
 
-  Fx256 tot_tor, tot_sabs;
+  using Acc = typename Tier::Acc;
+  constexpr int L = sizeof(Acc) / 8;  // limbs per accumulator; partials hold 2 L
+  Acc tot_tor, tot_sabs;
   fx_zero(tot_tor);
   fx_zero(tot_sabs);
   int flags = 0;
@@ -57,15 +59,15 @@ k_dfs(const double *__restrict__ B, const double *__restrict__ Blo, int k, const
   for (int g = 0; g < 2; ++g) {
     const int r1 = seg.r1[g];
     for (unsigned long long c = seg.c0[g] + gtid; c < seg.c1[g]; c += st) {
-      Sums Sm;
+      SumsOf<Acc> Sm;
       fx_zero(Sm.tor);
       fx_zero(Sm.sabs);
       Sm.flags = 0;
       walk_chunk<Tier>(src, k, r1, c, S, st, Sm, Q, blockDim.x);
       if (chunk_part && g == 0) {
-        unsigned long long *o = chunk_part + (size_t)(c - seg.c0[0]) * 8;
+        unsigned long long *o = chunk_part + (size_t)(c - seg.c0[0]) * 2 * L;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) { o[i] = Sm.tor.w[i]; o[4 + i] = Sm.sabs.w[i]; }
+        for (int i = 0; i < L; ++i) { o[i] = Sm.tor.w[i]; o[L + i] = Sm.sabs.w[i]; }
       }
       fx_add(tot_tor, Sm.tor);
       fx_add(tot_sabs, Sm.sabs);
@@ -75,45 +77,45 @@ k_dfs(const double *__restrict__ B, const double *__restrict__ Blo, int k, const
 
   // block reduction (exact, so the order does not matter) in the node slots' memory
   __syncthreads();
-  unsigned long long(*red)[8] = reinterpret_cast<unsigned long long(*)[8]>(smem);
+  unsigned long long(*red)[2 * L] = reinterpret_cast<unsigned long long(*)[2 * L]>(smem);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) { red[threadIdx.x][i] = tot_tor.w[i]; red[threadIdx.x][4 + i] = tot_sabs.w[i]; }
+  for (int i = 0; i < L; ++i) { red[threadIdx.x][i] = tot_tor.w[i]; red[threadIdx.x][L + i] = tot_sabs.w[i]; }
   if (flags) atomicOr(status, flags);
   __syncthreads();
   if (threadIdx.x == 0) {
-    Fx256 a, b, x;
+    Acc a, b, x;
     fx_zero(a);
     fx_zero(b);
     for (int t2 = 0; t2 < (int)blockDim.x; ++t2) {
-      for (int i = 0; i < 4; ++i) x.w[i] = red[t2][i];
+      for (int i = 0; i < L; ++i) x.w[i] = red[t2][i];
       fx_add(a, x);
-      for (int i = 0; i < 4; ++i) x.w[i] = red[t2][4 + i];
+      for (int i = 0; i < L; ++i) x.w[i] = red[t2][L + i];
       fx_add(b, x);
     }
-    for (int i = 0; i < 4; ++i) {
-      block_part[(size_t)blockIdx.x * 8 + i] = a.w[i];
-      block_part[(size_t)blockIdx.x * 8 + 4 + i] = b.w[i];
+    for (int i = 0; i < L; ++i) {
+      block_part[(size_t)blockIdx.x * 2 * L + i] = a.w[i];
+      block_part[(size_t)blockIdx.x * 2 * L + L + i] = b.w[i];
     }
   }
 }
 
+// sum of the blocks' partials (2 L limbs each) -> tor_result
+template <int L>
 __global__ void k_finalize(const unsigned long long *__restrict__ block_part, int nblocks, int k,
-                           int tier, const int *__restrict__ status, tor_result *__restrict__ out,
-                           unsigned long long *__restrict__ total8) {
+                           int tier, const int *__restrict__ status, tor_result *__restrict__ out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  Fx256 a, b, x;
+  FxW<L> a, b, x;
   fx_zero(a);
   fx_zero(b);
   for (int j = 0; j < nblocks; ++j) {
-    for (int i = 0; i < 4; ++i) x.w[i] = block_part[(size_t)j * 8 + i];
+    for (int i = 0; i < L; ++i) x.w[i] = block_part[(size_t)j * 2 * L + i];
     fx_add(a, x);
-    for (int i = 0; i < 4; ++i) x.w[i] = block_part[(size_t)j * 8 + 4 + i];
+    for (int i = 0; i < L; ++i) x.w[i] = block_part[(size_t)j * 2 * L + L + i];
     fx_add(b, x);
   }
-  unsigned long long w8[8];
-  for (int i = 0; i < 4; ++i) { w8[i] = a.w[i]; w8[4 + i] = b.w[i]; }
-  if (total8) for (int i = 0; i < 8; ++i) total8[i] = w8[i];
-  fixed_to_result(w8, k, tier, *status, out);
+  unsigned long long w[2 * L];
+  for (int i = 0; i < L; ++i) { w[i] = a.w[i]; w[L + i] = b.w[i]; }
+  fixed_to_result_w<L>(w, k, tier, *status, out);
 }
 
 // Independent DFMA chains; the result is consumed so the loop is not removed.
@@ -132,48 +134,65 @@ void launch_prep(const double *O, int k, int ld, int layout, double *B, double *
   k_prep<<<(n + 255) / 256, 256, 0, s>>>(O, k, ld, layout, B, Blo);
 }
 
+// elementwise 256-bit fixed-point products, as the 256-bit tier computes them
+__global__ void k_fx256_mul(const unsigned long long *__restrict__ a, const unsigned long long *__restrict__ b,
+                            int n, unsigned long long *__restrict__ out, int *__restrict__ ovf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  fx4 x, y;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) { x.w[j] = a[4 * (size_t)i + j]; y.w[j] = b[4 * (size_t)i + j]; }
+  int o = 0;
+  const fx4 r = fx4_mul(x, y, o);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) out[4 * (size_t)i + j] = r.w[j];
+  ovf[i] = o;
+}
+
+int launch_fx256_mul(const unsigned long long *a, const unsigned long long *b, int n, unsigned long long *out,
+                     int *ovf, cudaStream_t s) {
+  if (n > 0) k_fx256_mul<<<(n + 127) / 128, 128, 0, s>>>(a, b, n, out, ovf);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// calls f(Tier{}) with the walk tier of a TOR_PREC_* value
+template <class F>
+static void with_tier(int tier, F &&f) {
+  switch (tier) {
+    case TOR_PREC_DD: f(TierDD{}); break;
+    case TOR_PREC_FX128: f(TierFx<FX128_FRAC>{}); break;
+    case TOR_PREC_FX256: f(TierFx4{}); break;
+    default: f(TierF64{}); break;
+  }
+}
+
 void launch_dfs(int tier, int grid, int block, const double *B, const double *Blo, int k, const WalkSegs &seg,
                 double *scratch, unsigned long long *block_part, unsigned long long *chunk_part, int *status,
                 cudaStream_t s) {
-  if (tier == TOR_PREC_DD) {
-    const size_t sm = walk_smem_bytes<TierDD>(block);
-    cudaFuncSetAttribute(k_dfs<TierDD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_dfs<TierDD><<<grid, block, sm, s>>>(B, Blo, k, seg, scratch, block_part, chunk_part, status);
-  } else if (tier == TOR_PREC_FX128) {
-    using TF = TierFx<FX128_FRAC>;
-    const size_t sm = walk_smem_bytes<TF>(block);
-    cudaFuncSetAttribute(k_dfs<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_dfs<TF><<<grid, block, sm, s>>>(B, Blo, k, seg, scratch, block_part, chunk_part, status);
-  } else {
-    const size_t sm = walk_smem_bytes<TierF64>(block);
-    cudaFuncSetAttribute(k_dfs<TierF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_dfs<TierF64><<<grid, block, sm, s>>>(B, Blo, k, seg, scratch, block_part, chunk_part, status);
-  }
+  with_tier(tier, [&](auto t) {
+    using Tier = decltype(t);
+    const size_t sm = walk_smem_bytes<Tier>(block);
+    cudaFuncSetAttribute(k_dfs<Tier>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_dfs<Tier><<<grid, block, sm, s>>>(B, Blo, k, seg, scratch, block_part, chunk_part, status);
+  });
 }
 
 int dfs_max_blocks_per_sm(int tier, int block) {
   int n = 0;
-  cudaError_t e;
-  if (tier == TOR_PREC_DD) {
-    const size_t sm = walk_smem_bytes<TierDD>(block);
-    cudaFuncSetAttribute(k_dfs<TierDD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dfs<TierDD>, block, sm);
-  } else if (tier == TOR_PREC_FX128) {
-    using TF = TierFx<FX128_FRAC>;
-    const size_t sm = walk_smem_bytes<TF>(block);
-    cudaFuncSetAttribute(k_dfs<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dfs<TF>, block, sm);
-  } else {
-    const size_t sm = walk_smem_bytes<TierF64>(block);
-    cudaFuncSetAttribute(k_dfs<TierF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dfs<TierF64>, block, sm);
-  }
+  cudaError_t e = cudaSuccess;
+  with_tier(tier, [&](auto t) {
+    using Tier = decltype(t);
+    const size_t sm = walk_smem_bytes<Tier>(block);
+    cudaFuncSetAttribute(k_dfs<Tier>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dfs<Tier>, block, sm);
+  });
   return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
 void launch_finalize(const unsigned long long *block_part, int nblocks, int k, int tier,
-                     const int *status, tor_result *out, unsigned long long *total8, cudaStream_t s) {
-  k_finalize<<<1, 32, 0, s>>>(block_part, nblocks, k, tier, status, out, total8);
+                     const int *status, tor_result *out, cudaStream_t s) {
+  if (tier == TOR_PREC_FX256) k_finalize<6><<<1, 32, 0, s>>>(block_part, nblocks, k, tier, status, out);
+  else k_finalize<4><<<1, 32, 0, s>>>(block_part, nblocks, k, tier, status, out);
 }
 
 void launch_dfma_peak(double *sink, int grid, int block, int iters, cudaStream_t s) {
@@ -181,9 +200,12 @@ void launch_dfma_peak(double *sink, int grid, int block, int iters, cudaStream_t
 }
 
 int scratch_entries(int tier, int k, int r1) {
-  const int rreg = (tier == TOR_PREC_DD) ? TierDD::RREG
-                   : (tier == TOR_PREC_FX128) ? TierFx<FX128_FRAC>::RREG : TierF64::RREG;
-  const int w = (tier == TOR_PREC_FP64) ? 1 : 2;
+  int rreg = 0, w = 1;
+  with_tier(tier, [&](auto t) {
+    using Tier = decltype(t);
+    rreg = Tier::RREG;
+    w = Tier::W;
+  });
   const int a = sz(k), b = stack_entries(r1, rreg);
   return w * (a > b ? a : b);
 }

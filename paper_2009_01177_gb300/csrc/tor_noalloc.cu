@@ -95,7 +95,9 @@ int tor_single_noalloc(const double *O, int k, int ld, int layout, int prec, cud
     return e == cudaSuccess ? TOR_OK : nfail(TOR_ECUDA, "k = 0 result copy: %s", cudaGetErrorString(e));
   }
 
-  // the same chunking rule as tor_single's automatic choice
+  // chunks of at most 10 walked modes (up to 2^18 chunks): short per-thread
+  // stacks, so that the fixed array covers the largest k (the grid here is one
+  // 32-thread block per SM, so 2^k-10 chunks fill it long before 2^16)
   int d = k - 10;
   if (d > 18) d = 18;
   if (d < 0) d = 0;
@@ -124,7 +126,7 @@ int tor_single_noalloc(const double *O, int k, int ld, int layout, int prec, cud
   if (e != cudaSuccess) return nfail(TOR_ECUDA, "status clear: %s", cudaGetErrorString(e));
   tor::launch_dfs(prec, grid, NOALLOC_THREADS, B, Blo, k, tor::one_segment(r1, 0ull, 1ull << d), stack, part,
                   nullptr, status, stream);
-  tor::launch_finalize(part, grid, k, prec, status, out_dev, nullptr, stream);
+  tor::launch_finalize(part, grid, k, prec, status, out_dev, stream);
   e = cudaGetLastError();
   if (e != cudaSuccess) return nfail(TOR_ECUDA, "launch: %s", cudaGetErrorString(e));
   return TOR_OK;

@@ -56,7 +56,7 @@ struct SrcPattern {
 // stack S and eliminate the fixed modes in place; then the depth-first walk.
 template <class Tier, class Src>
 __device__ __forceinline__ void walk_chunk(const Src &src, int k, int r1, unsigned long long c, double *S,
-                                           size_t st, Sums &Sm, double *Q, size_t sq) {
+                                           size_t st, SumsOf<typename Tier::Acc> &Sm, double *Q, size_t sq) {
   using T = typename Tier::T;
   unsigned char pm[64];
   int np = 0;
@@ -87,10 +87,13 @@ __device__ __forceinline__ void walk_chunk(const Src &src, int k, int r1, unsign
   dfs_walk<Tier>(S, st, r1, t, np, k, Sm, Q, sq);
 }
 
-__host__ __device__ inline void fixed_to_result(const unsigned long long *w8, int k, int tier, int status,
-                                         tor_result *out) {
-  Fx256 a, b;
-  for (int i = 0; i < 4; ++i) { a.w[i] = w8[i]; b.w[i] = w8[4 + i]; }
+// Two L-limb fixed-point sums (signed sum, sum_abs; L/2 fraction limbs) ->
+// tor_result with the tier's error model
+template <int L>
+__host__ __device__ inline void fixed_to_result_w(const unsigned long long *w, int k, int tier, int status,
+                                                  tor_result *out) {
+  FxW<L> a, b;
+  for (int i = 0; i < L; ++i) { a.w[i] = w[i]; b.w[i] = w[L + i]; }
   double hi, lo;
   fx_to_dd(a, hi, lo);
   out->hi = hi;
@@ -99,6 +102,16 @@ __host__ __device__ inline void fixed_to_result(const unsigned long long *w8, in
   out->err_est = err_gamma(k) * unit_roundoff(tier) * out->sum_abs;
   out->tier = tier;
   out->status = (status & ST_NOTPD) ? TOR_ENOTPD : ((status & ST_RANGE) ? TOR_EINVAL : TOR_OK);
+}
+
+// limbs of one partial (signed sum and sum_abs) for a tier: 8, or 12 for the
+// 256-bit fixed-point tier
+__host__ __device__ inline int partial_limbs(int tier) { return tier == TOR_PREC_FX256 ? 12 : 8; }
+
+__host__ __device__ inline void fixed_to_result(const unsigned long long *w, int k, int tier, int status,
+                                                tor_result *out) {
+  if (tier == TOR_PREC_FX256) fixed_to_result_w<6>(w, k, tier, status, out);
+  else fixed_to_result_w<4>(w, k, tier, status, out);
 }
 
 }  // namespace tor

@@ -3,15 +3,15 @@
 The 2^d prefix chunks are independent and equal in cost (the paper's
 balanced partition, Algorithm 1), so rank r of R evaluates the contiguous
 chunk range [r 2^d / R, (r+1) 2^d / R) with tor_chunks and the ranks exchange
-one 256-bit fixed-point pair each.  Those partials add exactly (integer
-addition), so the gathered total is bit-identical to a single-GPU run.  The
-exchange is the only collective; it moves 64 bytes per rank.
+one fixed-point pair each (256-bit, or 384-bit for the 256-bit fixed-point
+tier).  Those partials add exactly (integer addition), so the gathered total
+is bit-identical to a single-GPU run.  The exchange is the only collective; it
+moves 64 (or 96) bytes per rank.
 """
 from __future__ import annotations
 
 import numpy as np
 
-MASK256 = (1 << 256) - 1
 
 
 def chunk_range(rank: int, world: int, nchunks: int):
@@ -21,41 +21,47 @@ def chunk_range(rank: int, world: int, nchunks: int):
     return rank * nchunks // world, (rank + 1) * nchunks // world
 
 
-def limbs_to_ints(limbs8):
-    """(signed sum, sum_abs) as Python integers modulo 2^256 from 8 little-endian 64-bit limbs."""
-    a = [int(x) & 0xFFFFFFFFFFFFFFFF for x in np.asarray(limbs8).ravel()]
-    lo = sum(a[i] << (64 * i) for i in range(4))
-    hi = sum(a[4 + i] << (64 * i) for i in range(4))
+def limbs_to_ints(limbs):
+    """(signed sum, sum_abs) as Python integers modulo 2^(64 L) from 2 L little-endian 64-bit
+    limbs (L = 4, or 6 for the 256-bit fixed-point tier)."""
+    a = [int(x) & 0xFFFFFFFFFFFFFFFF for x in np.asarray(limbs).ravel()]
+    L = len(a) // 2
+    lo = sum(a[i] << (64 * i) for i in range(L))
+    hi = sum(a[L + i] << (64 * i) for i in range(L))
     return lo, hi
 
 
-def ints_to_limbs(lo: int, hi: int) -> np.ndarray:
-    out = np.zeros(8, dtype=np.uint64)
-    lo &= MASK256
-    hi &= MASK256
-    for i in range(4):
+def ints_to_limbs(lo: int, hi: int, limbs: int = 8) -> np.ndarray:
+    L = limbs // 2
+    mask = (1 << (64 * L)) - 1
+    out = np.zeros(limbs, dtype=np.uint64)
+    lo &= mask
+    hi &= mask
+    for i in range(L):
         out[i] = (lo >> (64 * i)) & 0xFFFFFFFFFFFFFFFF
-        out[4 + i] = (hi >> (64 * i)) & 0xFFFFFFFFFFFFFFFF
+        out[L + i] = (hi >> (64 * i)) & 0xFFFFFFFFFFFFFFFF
     return out
 
 
 def sum_partials(rows) -> np.ndarray:
-    """Exact sum of several 8-limb partials (rows of an (n, 8) array)."""
+    """Exact sum of several partials (rows of an (n, 8) or (n, 12) array)."""
+    rows = np.asarray(rows)
+    limbs = rows.shape[-1] if rows.ndim > 1 else rows.size
     lo = hi = 0
-    for r in np.asarray(rows).reshape(-1, 8):
+    for r in rows.reshape(-1, limbs):
         a, b = limbs_to_ints(r)
         lo, hi = lo + a, hi + b
-    return ints_to_limbs(lo, hi)
+    return ints_to_limbs(lo, hi, limbs)
 
 
-def gather_partials(local8, group=None) -> np.ndarray:
+def gather_partials(local, group=None) -> np.ndarray:
     """All-gather each rank's 8-limb partial and add them exactly (any backend)."""
     import torch
     import torch.distributed as dist
     world = dist.get_world_size(group)
     backend = dist.get_backend(group)
     dev = torch.device("cuda", torch.cuda.current_device()) if backend == "nccl" else torch.device("cpu")
-    mine = torch.from_numpy(np.asarray(local8, dtype=np.uint64).view(np.int64).copy()).to(dev)
+    mine = torch.from_numpy(np.asarray(local, dtype=np.uint64).view(np.int64).copy()).to(dev)
     bufs = [torch.empty_like(mine) for _ in range(world)]
     dist.all_gather(bufs, mine, group=group)
     return sum_partials(np.stack([b.cpu().numpy().view(np.uint64) for b in bufs]))
@@ -68,7 +74,7 @@ def tor_sharded(ctx, O, chunk_bits: int, prec: str = "fp64", group=None):
     rank, world = dist.get_rank(group), dist.get_world_size(group)
     lo, hi = chunk_range(rank, world, 1 << chunk_bits)
     part = ctx.chunks(O, chunk_bits, lo, hi, prec=prec).cpu().numpy().view(np.uint64)
-    local = sum_partials(part) if part.size else np.zeros(8, dtype=np.uint64)
+    local = sum_partials(part) if part.size else np.zeros(tor.partial_limbs(prec), dtype=np.uint64)
     total = gather_partials(local, group)
     k = O.shape[0] // 2
     return tor.fixed_to_result([int(x) for x in total], k, prec), total

@@ -18,9 +18,14 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtorontonian.so")
 
 TOR_OK, TOR_EINVAL, TOR_ENOTPD, TOR_ECUDA, TOR_ETIMEOUT, TOR_EPREC, TOR_ENOMEM = range(7)
-PREC_AUTO, PREC_FP64, PREC_DD, PREC_FX128 = 0, 1, 2, 3
+PREC_AUTO, PREC_FP64, PREC_DD, PREC_FX128, PREC_FX256 = 0, 1, 2, 3, 4
 LAYOUT_XXPP, LAYOUT_XPXP = 0, 1
-_PREC = {"auto": PREC_AUTO, "fp64": PREC_FP64, "dd": PREC_DD, "fx128": PREC_FX128}
+_PREC = {"auto": PREC_AUTO, "fp64": PREC_FP64, "dd": PREC_DD, "fx128": PREC_FX128, "fx256": PREC_FX256}
+
+
+def partial_limbs(prec: str) -> int:
+    """64-bit limbs of one chunk partial: two 256-bit sums, or two 384-bit sums for fx256."""
+    return 12 if prec == "fx256" else 8
 _LAYOUT = {"xxpp": LAYOUT_XXPP, "xpxp": LAYOUT_XPXP}
 
 
@@ -86,6 +91,7 @@ SIGNATURES = {
     "tor_single_async": (_I, [_VP, _VP, _I, _I, _I, _I, _VP, _VP]),
     "tor_chunks": (_I, [_VP, _VP, _I, _I, _I, _I, _I, _U64, _U64, _VP, _VP]),
     "tor_fixed_to_result": (_I, [ctypes.POINTER(_U64), _I, _I, ctypes.POINTER(TorResultC)]),
+    "tor_fx256_mul": (_I, [_VP, _VP, _I, _VP, _VP, _VP]),
     "tor_batch": (_I, [_VP, _VP, _VP, _VP, _I, _I, _I, _D, _VP, _VP]),
     "tor_bounds": (_I, [_VP, _VP, _VP, _VP, _I, _I, _D, _VP, _VP]),
     "tor_batch_reserve": (_I, [_VP, _I, _I]),
@@ -224,9 +230,10 @@ class Context:
 
     def chunks(self, O: torch.Tensor, chunk_bits: int, c_begin: int, c_end: int, prec: str = "fp64",
                layout: str = "xxpp", stream=None) -> torch.Tensor:
-        """Exact per-chunk partials, an int64 CUDA tensor (c_end - c_begin, 8) of raw limbs."""
+        """Exact per-chunk partials, an int64 CUDA tensor (c_end - c_begin, 8) of raw limbs
+        ((c_end - c_begin, 12) for fx256)."""
         k, ld = _mat(O)
-        part = torch.zeros((max(c_end - c_begin, 0), 8), dtype=torch.int64, device=O.device)
+        part = torch.zeros((max(c_end - c_begin, 0), partial_limbs(prec)), dtype=torch.int64, device=O.device)
         _check(self.lib.tor_chunks(self.h, O.data_ptr(), k, ld, _LAYOUT[layout], _PREC[prec],
                                    chunk_bits, c_begin, c_end, _stream(stream), part.data_ptr()))
         return part
@@ -345,21 +352,40 @@ def single_noalloc(O: torch.Tensor, out: torch.Tensor, prec: str = "fp64", layou
                                              _stream(stream), out.data_ptr()))
 
 
-def fixed_to_result(limbs8, k: int, tier: str = "fp64") -> TorResult:
-    """Convert 8 raw limbs (signed sum, sum_abs; 256-bit fixed point, 128 fraction bits)."""
-    arr = (ctypes.c_uint64 * 8)(*[int(x) & 0xFFFFFFFFFFFFFFFF for x in limbs8])
+def fixed_to_result(limbs, k: int, tier: str = "fp64") -> TorResult:
+    """Convert raw limbs (signed sum, sum_abs): 8 limbs of 256-bit fixed point with 128 fraction
+    bits, or 12 limbs of 384-bit fixed point with 192 fraction bits for fx256."""
+    n = partial_limbs(tier)
+    limbs = list(limbs)
+    if len(limbs) != n:
+        raise ValueError(f"{tier} partials have {n} limbs, got {len(limbs)}")
+    arr = (ctypes.c_uint64 * n)(*[int(x) & 0xFFFFFFFFFFFFFFFF for x in limbs])
     out = TorResultC()
     _check(load_library().tor_fixed_to_result(arr, k, _PREC[tier], ctypes.byref(out)))
     return TorResult.from_c(out)
 
 
-def limbs_to_int(limbs4) -> int:
-    """Signed Python integer of 4 little-endian 64-bit limbs (value = int / 2^128)."""
+def fx256_mul(a: torch.Tensor, b: torch.Tensor):
+    """Elementwise 256-bit fixed-point products as the fx256 tier forms them: a, b int64 CUDA
+    tensors (n, 4) of little-endian limbs (value / 2^192); returns (products (n, 4), overflow (n,))."""
+    n = a.shape[0]
+    out = torch.zeros_like(a)
+    ovf = torch.zeros(n, dtype=torch.int32, device=a.device)
+    _check(load_library().tor_fx256_mul(a.data_ptr(), b.data_ptr(), n, out.data_ptr(), ovf.data_ptr(), None))
+    torch.cuda.synchronize(a.device)
+    return out, ovf
+
+
+def limbs_to_int(limbs) -> int:
+    """Signed Python integer of L little-endian 64-bit limbs (value = int / 2^(32 L): 4 limbs
+    with 128 fraction bits, or 6 limbs with 192 for fx256)."""
+    limbs = list(limbs)
     v = 0
-    for i, x in enumerate(limbs4):
+    for i, x in enumerate(limbs):
         v |= (int(x) & 0xFFFFFFFFFFFFFFFF) << (64 * i)
-    if v >> 255:
-        v -= 1 << 256
+    nb = 64 * len(limbs)
+    if v >> (nb - 1):
+        v -= 1 << nb
     return v
 
 

@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -69,3 +70,34 @@ def test_fixed_point_conversion_on_host(lib):
     limbs = [(v >> (64 * i)) & 0xFFFFFFFFFFFFFFFF for i in range(4)] + [0, 0, 1, 0]
     r = tor.fixed_to_result(limbs, 5)
     assert (r.hi, r.lo) == (1.0, 2.0 ** -100)
+
+
+def test_fixed_point_conversion_of_384_bit_partials(lib):
+    # the 256-bit tier's partials: two 6-limb values with 192 fraction bits
+    from paper_2009_01177_gb300 import tor
+    tor.load_library()
+
+    def limbs6(v):
+        v &= (1 << 384) - 1
+        return [(v >> (64 * i)) & 0xFFFFFFFFFFFFFFFF for i in range(6)]
+
+    r = tor.fixed_to_result(limbs6(3 << 192) + limbs6(5 << 192), 7, "fx256")
+    assert (r.hi, r.lo, r.sum_abs, r.tier) == (3.0, 0.0, 5.0, 4)
+    # -(2^-100 + 2^-190): its low part lies far below the 128-bit tiers' resolution
+    v = -((1 << 92) + (1 << 2))
+    r = tor.fixed_to_result(limbs6(v) + limbs6(1 << 192), 7, "fx256")
+    assert (r.hi, r.lo) == (-(2.0 ** -100), -(2.0 ** -190))
+    # error model: 4k u sum_abs with u = 2^-186
+    assert r.err_est == 4 * 7 * 2.0 ** -186 * 1.0
+    with pytest.raises(ValueError):
+        tor.fixed_to_result(limbs6(1) + limbs6(1), 7, "fp64")   # 12 limbs given, 8 expected
+
+
+def test_shard_sums_of_384_bit_partials():
+    from paper_2009_01177_gb300 import shard
+    a = shard.ints_to_limbs(-(1 << 300), 1 << 300, limbs=12)
+    b = shard.ints_to_limbs(3, 7, limbs=12)
+    tot = shard.sum_partials(np.stack([a, b]))
+    assert tot.shape == (12,)
+    lo, hi = shard.limbs_to_ints(tot)
+    assert lo == (3 - (1 << 300)) % (1 << 384) and hi == (1 << 300) + 7

@@ -40,8 +40,10 @@ def test_bounds_match_reference_formulas(ctx):
         ref = reference_bound(O, 1e-10)
         for key in ("log_tmax", "log_tor_est", "log_kappa_est", "bits_needed"):
             assert abs(g[key] - ref[key]) <= 1e-3 * max(1.0, abs(ref[key])), (key, g[key], ref[key])
-        fx_ok = ref["log_tmax"] <= 11 * math.log(2) and ref["bits_needed"] <= 120
-        assert g["tier"] == (1 if ref["bits_needed"] <= 72 else (3 if fx_ok else 2))
+        bits, lt = ref["bits_needed"], ref["log_tmax"] / math.log(2)
+        want = (1 if bits <= 72 else 3 if (lt <= 11 and bits <= 120) else 2 if bits <= 124
+                else 4 if lt <= 30 else 2)
+        assert g["tier"] == want, (bits, lt, g["tier"])
 
 
 def test_bounds_thermal_are_exact_estimates(ctx):

@@ -136,7 +136,7 @@ def test_sharded_chunks_add_up_exactly(ctx):
 _K32_CHUNK_REF = {}
 
 
-@pytest.mark.parametrize("prec", ["fp64", "dd", "fx128"])
+@pytest.mark.parametrize("prec", ["fp64", "dd", "fx128", "fx256"])
 def test_k32_sampled_chunks_at_bench_depth(ctx, prec):
     # the benchmark's instance at its autotuned chunk depth (d = 16: 2^16 chunks of 2^16
     # subsets): one chunk with none of the 16 fixed modes in Z and one with all of them
@@ -145,16 +145,17 @@ def test_k32_sampled_chunks_at_bench_depth(ctx, prec):
     st, pat, O = gi.workload_m100(32)
     Od = dev(O)
     k, d = 32, 16
-    u = {"fp64": 2.0 ** -53, "dd": 2.0 ** -104, "fx128": 2.0 ** -100}[prec]
+    u = {"fp64": 2.0 ** -53, "dd": 2.0 ** -104, "fx128": 2.0 ** -100, "fx256": 2.0 ** -186}[prec]
     for c in (0x0000, 0xFFFF):
         if c not in _K32_CHUNK_REF:
-            _K32_CHUNK_REF[c] = oracle.tor_range(O, c << (k - d), (c + 1) << (k - d))
-        ref = _K32_CHUNK_REF[c]
+            _K32_CHUNK_REF[c] = oracle.tor_exact(O, c << (k - d), (c + 1) << (k - d))
+        ref_t, ref_s = _K32_CHUNK_REF[c]
         part = ctx.chunks(Od, d, c, c + 1, prec=prec).cpu().numpy()[0]
-        got = Fraction(limbs_to_int(part[:4]), 1 << 128)
-        sabs = Fraction(limbs_to_int(part[4:]), 1 << 128)
-        assert abs(float(sabs) - ref.sum_abs) <= 1e-12 * ref.sum_abs, c
-        assert abs(float(got - Fraction(ref.hi) - Fraction(ref.lo))) <= 4 * k * u * ref.sum_abs, c
+        L = part.size // 2
+        got = Fraction(limbs_to_int(part[:L]), 1 << (32 * L))
+        sabs = Fraction(limbs_to_int(part[L:]), 1 << (32 * L))
+        assert abs(sabs - ref_s) <= Fraction(1e-12) * ref_s, c
+        assert abs(got - ref_t) <= 4 * k * Fraction(u) * ref_s + ref_s * Fraction(1, 2 ** 190), c
 
 
 def test_launch_shape_does_not_change_bits(ctx):
@@ -341,3 +342,117 @@ def test_fx128_rejects_out_of_range(ctx, cuda_lib):
     with pytest.raises(cuda_lib.TorError) as ei:
         ctx.single(dev(O), prec="fx128")
     assert ei.value.code == cuda_lib.TOR_EINVAL
+
+
+# ------------------------------------------------------- 256-bit fixed point
+def _fx256_reference(a: int, b: int):
+    """The 256-bit tier's product, restated on Python integers: magnitudes, the limb products
+    a_i b_j of columns 3 and up plus the high halves of column 2 (only carries out of columns
+    0..2 are dropped), shifted down by 192 bits, sign restored; and whether it overflows."""
+    ua, ub = abs(a), abs(b)
+    x = [(ua >> (64 * i)) & (2 ** 64 - 1) for i in range(4)]
+    y = [(ub >> (64 * i)) & (2 ** 64 - 1) for i in range(4)]
+    acc = 0
+    for i in range(4):
+        for j in range(4):
+            p = x[i] * y[j]
+            if i + j >= 3:
+                acc += p << (64 * (i + j))
+            elif i + j == 2:
+                acc += (p >> 64) << (64 * 3)
+    q = acc >> 192
+    ovf = q >> 255 != 0
+    q &= (1 << 256) - 1
+    return (-q if (a < 0) != (b < 0) else q), ovf
+
+
+def _to_limbs4(v: int):
+    v &= (1 << 256) - 1
+    return [((v >> (64 * i)) & (2 ** 64 - 1)) for i in range(4)]
+
+
+def _from_limbs4(w):
+    v = sum((int(x) & (2 ** 64 - 1)) << (64 * i) for i, x in enumerate(w))
+    return v - (1 << 256) if v >> 255 else v
+
+
+def test_fx256_mul_matches_big_integer_definition(cuda_lib):
+    rng = np.random.default_rng(5)
+    vals = []
+    for _ in range(3000):
+        nbits = int(rng.integers(1, 255))          # magnitudes from 2^-191 to 2^62
+        m = int.from_bytes(rng.bytes(32), "little") % (1 << nbits)
+        vals.append(-m if rng.random() < 0.5 else m)
+    vals += [0, 1, -1, (1 << 192), -(1 << 192), (1 << 254), (1 << 255) - 1, 3 << 192]
+    a_v = vals
+    b_v = list(reversed(vals))
+    A = torch.from_numpy(np.array([_to_limbs4(v) for v in a_v], dtype=np.uint64).view(np.int64)).cuda()
+    B = torch.from_numpy(np.array([_to_limbs4(v) for v in b_v], dtype=np.uint64).view(np.int64)).cuda()
+    out, ovf = cuda_lib.fx256_mul(A, B)
+    out = out.cpu().numpy().view(np.uint64)
+    ovf = ovf.cpu().numpy()
+    checked = 0
+    for i, (a, b) in enumerate(zip(a_v, b_v)):
+        ref, ref_ovf = _fx256_reference(a, b)
+        assert bool(ovf[i]) == ref_ovf, i
+        if ref_ovf:
+            continue
+        got = _from_limbs4(out[i])
+        assert got == ref, (i, a, b)
+        exact = abs(a * b) >> 192                  # the dropped carries cost at most a few units
+        assert 0 <= exact - abs(got) <= 6, i
+        checked += 1
+    assert checked > 2900
+
+
+def _fx256_chunk_total(ctx, Od, k, d):
+    from paper_2009_01177_gb300 import shard
+    part = ctx.chunks(Od, d, 0, 1 << d, prec="fx256").cpu().numpy().view(np.uint64)
+    lo, hi = shard.limbs_to_ints(shard.sum_partials(part))
+    sgn = lambda v: v - (1 << 384) if v >> 383 else v
+    return Fraction(sgn(lo), 1 << 192), Fraction(hi, 1 << 192)
+
+
+@pytest.mark.parametrize("k", [1, 4, 9, 13])
+def test_fx256_thermal_closed_form(ctx, k):
+    Od = dev(gi.thermal_O(k, 0.25))
+    tor_x, sabs_x = _fx256_chunk_total(ctx, Od, k, min(k, 3))
+    bound = 4 * k * Fraction(1, 2 ** 186) * sabs_x
+    assert abs(tor_x - Fraction(1, 3) ** k) <= bound
+    r = ctx.single(Od, prec="fx256")
+    assert r.tier == 4 and r.status == 0
+    assert abs(Fraction(r.hi) + Fraction(r.lo) - Fraction(1, 3) ** k) <= Fraction(r.err_est) + Fraction(1, 3) ** k * Fraction(1, 2 ** 104)
+
+
+@pytest.mark.parametrize("k", [8, 12, 15])
+def test_fx256_against_the_exact_oracle(ctx, k):
+    st, pat, O32 = gi.workload_m100(32)
+    O = gi.select(st.O, pat[:k])
+    ref_t, ref_s = oracle.tor_exact(O)
+    got_t, got_s = _fx256_chunk_total(ctx, dev(O), k, 4)
+    # both sides: a few units of 2^-192 / 2^-200 per term; the GPU bound 4k 2^-186 sum t covers both
+    assert abs(got_t - ref_t) <= 4 * k * Fraction(1, 2 ** 186) * ref_s
+    assert abs(got_s - ref_s) <= 4 * k * Fraction(1, 2 ** 186) * ref_s
+    # kappa up to 1e16 here: the relative error stays near 2^-186 kappa, far below 1e-20
+    assert abs((got_t - ref_t) / ref_t) < 1e-20
+
+
+def test_auto_routes_beyond_double_double_to_256_bits(ctx):
+    # k = 20 of the M = 100 state: kappa = 1.2e19, so tol = 1e-25 needs about 150 bits
+    st, pat, O32 = gi.workload_m100(32)
+    O = gi.select(st.O, pat[:20])
+    ref_t, ref_s = oracle.tor_exact(O)
+    r = ctx.single(dev(O), prec="auto", tol=1e-25)
+    assert r.tier == 4 and r.status == 0
+    err = abs(Fraction(r.hi) + Fraction(r.lo) - ref_t)
+    assert err <= Fraction(r.err_est) + abs(ref_t) * Fraction(1, 2 ** 104)
+    assert r.err_est <= 1e-25 * abs(float(ref_t))
+
+
+def test_fx256_rejects_out_of_range(ctx, cuda_lib):
+    O = 0.99 * np.eye(40)      # t_max = 10^40 > 2^30
+    with pytest.raises(cuda_lib.TorError) as ei:
+        ctx.single(dev(O), prec="fx256")
+    assert ei.value.code == cuda_lib.TOR_EINVAL
+    with pytest.raises(cuda_lib.TorError):
+        ctx.batch([dev(gi.thermal_O(3, 0.25))], prec="fx256")     # batches have no 256-bit tier

@@ -197,3 +197,39 @@ def test_pins_catch_planted_mistakes():
     # 5 drops the first elimination update, 6 sums sqrt(det) instead of 1/sqrt(det)
     for mutation in range(1, 7):
         assert _quick_pins(mutation), f"mutation {mutation} not caught"
+
+
+# ---- the exact (raw fixed-point) output, used to check the 256-bit GPU tier
+@pytest.mark.parametrize("k", [1, 5, 9, 12])
+def test_exact_output_thermal_closed_form(k):
+    # O = I/4: Tor = (1/3)^k and sum t = (7/3)^k; the fixed-point evaluation must
+    # land within a few 2^-200 units per term, far below the double-double output
+    tor_x, sabs_x = oracle.tor_exact(gi.thermal_O(k, 0.25))
+    sabs = Fraction(7, 3) ** k
+    assert abs(tor_x - Fraction(1, 3) ** k) <= Fraction(1, 2 ** 195) * sabs
+    assert abs(sabs_x - sabs) <= Fraction(1, 2 ** 195) * sabs
+
+
+@pytest.mark.parametrize("k1,k2,seed", [(3, 4, 21), (4, 5, 22)])
+def test_exact_output_block_factorisation(k1, k2, seed):
+    # Tor(O1 (+) O2) = Tor(O1) Tor(O2) to the full fixed-point precision
+    st = gi.lossy_gbs_state(k1 + k2, 0.6, 1.2, 0.5, seed)
+    pat = np.arange(k1 + k2)
+    O1, O2 = gi.select(st.O, pat[:k1]), gi.select(st.O, pat[k1:])
+    t1, s1 = oracle.tor_exact(O1)
+    t2, s2 = oracle.tor_exact(O2)
+    t12, s12 = oracle.tor_exact(gi.block_diag_modes(O1, O2))
+    assert abs(t12 - t1 * t2) <= Fraction(1, 2 ** 190) * s12
+    assert abs(s12 - s1 * s2) <= Fraction(1, 2 ** 190) * s12
+
+
+def test_exact_output_agrees_with_the_double_double_output():
+    st, pat, O = gi.workload_m16_k10()
+    ref = oracle.tor(O)
+    tor_x, sabs_x = oracle.tor_exact(O)
+    assert abs(Fraction(ref.hi) + Fraction(ref.lo) - tor_x) <= Fraction(1, 2 ** 104) * abs(tor_x)
+    assert abs(Fraction(ref.sum_abs) + Fraction(ref.sum_abs_lo) - sabs_x) <= Fraction(1, 2 ** 104) * sabs_x
+    # and a mask range is the sum of its halves, exactly
+    a = oracle.tor_exact(O, 0, 300)
+    b = oracle.tor_exact(O, 300, 1 << 10)
+    assert (a[0] + b[0], a[1] + b[1]) == (tor_x, sabs_x)
