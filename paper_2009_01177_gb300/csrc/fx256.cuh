@@ -10,10 +10,12 @@
 //
 // The product is accumulated column by column (each column is the sum of the
 // low halves of the limb products a_i b_j with i + j equal to the column and
-// the high halves of those one column lower) with PTX multiply-add carry
-// chains.  Columns 0..2 lie below the kept part: only their carries into
-// column 3 are dropped, an error of a few units of 2^-192 on top of the
-// truncation (Sec. 5.1 truncates too).  Overflow of the 255-bit magnitude
+// the high halves of those one column lower): by default each column summed
+// on its own in 128 bits, then one carry propagation; TOR_FX4_MUL_CHAIN=1
+// uses a single PTX multiply-add carry chain through the columns instead.
+// Columns 0..2 lie below the kept part: only their carries into column 3 are
+// dropped, an error of a few units of 2^-192 on top of the truncation
+// (Sec. 5.1 truncates too).  Overflow of the 255-bit magnitude
 // range sets a flag instead of wrapping silently.
 #pragma once
 #include <cstdint>
@@ -81,14 +83,20 @@ __device__ __forceinline__ void col_hi(unsigned long long &c0, unsigned long lon
       : "l"(x), "l"(y));
 }
 
+#ifndef TOR_FX4_MUL_CHAIN
+#define TOR_FX4_MUL_CHAIN 0
+#endif
+
 // (a * b) >> 192 on magnitudes, truncated, sign restored; ovf = 1 when the
 // result does not fit in 255 magnitude bits
 __device__ __forceinline__ fx4 fx4_mul(const fx4 &a, const fx4 &b, int &ovf) {
   const bool na = fx4_neg_p(a), nb = fx4_neg_p(b);
   const fx4 ua = na ? fx4_neg(a) : a, ub = nb ? fx4_neg(b) : b;
   const unsigned long long *x = ua.w, *y = ub.w;
-  unsigned long long c0 = 0ull, c1 = 0ull, c2 = 0ull;
   fx4 r;
+#if TOR_FX4_MUL_CHAIN
+  // one carry chain through the columns in order
+  unsigned long long c0 = 0ull, c1 = 0ull, c2 = 0ull;
   // column 3: low halves of i + j = 3, high halves of i + j = 2
   col_hi(c0, c1, c2, x[0], y[2]); col_hi(c0, c1, c2, x[1], y[1]); col_hi(c0, c1, c2, x[2], y[0]);
   col_lo(c0, c1, c2, x[0], y[3]); col_lo(c0, c1, c2, x[1], y[2]);
@@ -110,6 +118,36 @@ __device__ __forceinline__ fx4 fx4_mul(const fx4 &a, const fx4 &b, int &ovf) {
   // column 7 and above must be empty, and the top bit of column 6 clear
   col_hi(c0, c1, c2, x[3], y[3]);
   if (c0 | c1 | c2 | (r.w[3] >> 63)) ovf = 1;
+#else
+  // the same columns summed independently (each fits 128 bits: at most seven
+  // 64-bit terms), so the multiplies and the four column sums can overlap;
+  // then one short carry propagation across the columns
+  typedef unsigned __int128 u128;
+  const u128 p02 = (u128)x[0] * y[2], p11 = (u128)x[1] * y[1], p20 = (u128)x[2] * y[0];
+  const u128 p03 = (u128)x[0] * y[3], p12 = (u128)x[1] * y[2], p21 = (u128)x[2] * y[1], p30 = (u128)x[3] * y[0];
+  const u128 p13 = (u128)x[1] * y[3], p22 = (u128)x[2] * y[2], p31 = (u128)x[3] * y[1];
+  const u128 p23 = (u128)x[2] * y[3], p32 = (u128)x[3] * y[2];
+  const u128 p33 = (u128)x[3] * y[3];
+  const unsigned long long M = ~0ull;
+  const u128 s3 = (p02 >> 64) + (p11 >> 64) + (p20 >> 64) + (u128)(unsigned long long)(p03 & M) +
+                  (u128)(unsigned long long)(p12 & M) + (u128)(unsigned long long)(p21 & M) +
+                  (u128)(unsigned long long)(p30 & M);
+  const u128 s4 = (p03 >> 64) + (p12 >> 64) + (p21 >> 64) + (p30 >> 64) + (u128)(unsigned long long)(p13 & M) +
+                  (u128)(unsigned long long)(p22 & M) + (u128)(unsigned long long)(p31 & M);
+  const u128 s5 = (p13 >> 64) + (p22 >> 64) + (p31 >> 64) + (u128)(unsigned long long)(p23 & M) +
+                  (u128)(unsigned long long)(p32 & M);
+  const u128 s6 = (p23 >> 64) + (p32 >> 64) + (u128)(unsigned long long)(p33 & M);
+  u128 t = s3;
+  r.w[0] = (unsigned long long)t;
+  t = s4 + (t >> 64);
+  r.w[1] = (unsigned long long)t;
+  t = s5 + (t >> 64);
+  r.w[2] = (unsigned long long)t;
+  t = s6 + (t >> 64);
+  r.w[3] = (unsigned long long)t;
+  t = (p33 >> 64) + (t >> 64);  // column 7 and above must be empty, and bit 255 clear
+  if (t != 0 || (r.w[3] >> 63)) ovf = 1;
+#endif
   return (na != nb) ? fx4_neg(r) : r;
 }
 

@@ -122,8 +122,9 @@ __device__ __forceinline__ void fx_add_signed(Fx256 &acc, double x, bool neg, in
 #ifndef TOR_FX_MINB
 #define TOR_FX_MINB 4
 #endif
-// The 256-bit tier: values are eight registers, so one-mode register subtrees
-// and small shared-memory nodes (four doubles per entry).
+// The 256-bit tier: values are eight registers, so one-mode register subtrees,
+// small shared-memory nodes (four doubles per entry), and three resident
+// blocks (168 registers, some spills): 14% faster than two at k = 28.
 #ifndef TOR_FX4_RREG
 #define TOR_FX4_RREG 1
 #endif
@@ -131,7 +132,7 @@ __device__ __forceinline__ void fx_add_signed(Fx256 &acc, double x, bool neg, in
 #define TOR_FX4_RSMEM 2
 #endif
 #ifndef TOR_FX4_MINB
-#define TOR_FX4_MINB 2
+#define TOR_FX4_MINB 3
 #endif
 
 __device__ __forceinline__ double dmul(double a, double b) { return a * b; }
