@@ -379,17 +379,29 @@ def run_mh(args):
                 record.append(ch["pat"].clone())
         return float(acc) / steps
 
-    def train(net, pats, w, iters, batch, lr, val=None):
-        """Adam on the weighted NLL; with val, keep the parameters of best validation NLL."""
+    def train(net, pats, w, iters, batch, lr, val=None, val_w=None, resample=False):
+        """Adam on the weighted NLL; with val, keep the parameters of best validation NLL
+        (weighted by val_w when given).  resample: draw each batch with probability
+        proportional to w and unit weights (the same expected gradient, less variance
+        when the weights are heavy-tailed)."""
         best, best_theta, nll0 = None, None, None
+
+        def val_nll():
+            lq = net.logq(val)
+            return float(-(lq * val_w).sum() / val_w.sum()) if val_w is not None else float(-lq.mean())
         if val is not None:
-            nll0 = best = float(-net.logq(val).mean())
+            nll0 = best = val_nll()
             best_theta = net.get_params(0)
+        ones = torch.ones(batch, dtype=torch.float32, device="cuda")
         for it in range(iters):
-            idx = torch.randint(0, pats.shape[0], (batch,), device="cuda")
-            net.train_step(pats[idx].contiguous(), w[idx].contiguous(), lr=lr)
+            if resample:
+                idx = torch.multinomial(w, batch, replacement=True)
+                net.train_step(pats[idx].contiguous(), ones, lr=lr)
+            else:
+                idx = torch.randint(0, pats.shape[0], (batch,), device="cuda")
+                net.train_step(pats[idx].contiguous(), w[idx].contiguous(), lr=lr)
             if val is not None and (it + 1) % 200 == 0:
-                v = float(-net.logq(val).mean())
+                v = val_nll()
                 if v < best:
                     best, best_theta = v, net.get_params(0)
         if val is not None:
@@ -414,9 +426,41 @@ def run_mh(args):
     net.set_marginals(marg60)                 # start at the plain proposal
     nll_plain, nll_learned = train(net, trn, torch.ones(trn.shape[0], dtype=torch.float32, device="cuda"),
                                    3000, 4096, 3e-4, val=val)
+    # the same network trained instead on importance-weighted pairs the exact kernel scored:
+    # proposals of the plain product proposal with weights p(S)/q(S), self-normalised
+    progress("importance-weighted pairs")
+    rng = np.random.default_rng(61)
+    X = (rng.random((48 * C, st.M)) < marg60).astype(np.uint8)
+    X = X[X.sum(1) <= k_cap]
+    O60 = torch.from_numpy(st.O).cuda()
+    Pis = tor.pack_patterns(X, st.M).cuda()
+    ois = torch.zeros(X.shape[0] * tor.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    t_is = time.perf_counter()
+    ctx.batch_patterns_async(O60, Pis, ois, prec="fp64")
+    torch.cuda.synchronize()
+    t_is = time.perf_counter() - t_is
+    ris = tor.results_array(ois, X.shape[0])
+    tor_v = ris["hi"] + ris["lo"]
+    ok = (ris["status"] == 0) & (tor_v > 0)
+    logdet60 = float(np.linalg.slogdet(st.Sigma)[1])
+    logp_is = np.log(np.where(ok, tor_v, 1.0)) - 0.5 * logdet60
+    logq_is = (X * np.log(marg60) + (1 - X) * np.log1p(-marg60)).sum(1)
+    lw = np.where(ok, logp_is - logq_is, -np.inf)
+    w_is = np.exp(lw - lw.max())
+    w_is /= w_is.sum()
+    ess_is = float(1.0 / (w_is ** 2).sum())
+    perm = rng.permutation(X.shape[0])
+    nv = X.shape[0] // 10
+    wt = torch.tensor(w_is, dtype=torch.float32, device="cuda")
+    vi, ti = torch.from_numpy(perm[:nv]).cuda(), torch.from_numpy(perm[nv:]).cuda()
+    net_is = tor.MLP(ctx, st.M, 256, seed=6)
+    net_is.set_marginals(marg60)
+    progress(f"training on {X.shape[0]} weighted pairs (weight ESS {ess_is:.0f})")
+    nll_is0, nll_is = train(net_is, Pis[ti].contiguous(), wt[ti].contiguous(), 3000, 4096, 3e-4,
+                            val=Pis[vi].contiguous(), val_w=wt[vi].double().contiguous(), resample=True)
     res = {}
     steps = max(8, 4 * args.steps)
-    for name, prop in (("plain", None), ("learned", net)):
+    for name, prop in (("plain", None), ("learned", net), ("learned_is", net_is)):
         progress(f"race: {name}")
         chn = chains(st)
         run(chn, 3, 7, prop, k_cap=k_cap)
@@ -435,12 +479,20 @@ def run_mh(args):
            "learned": res["learned"],
            "speedup_accepted": res["learned"]["accepted_samples_per_s"] / res["plain"]["accepted_samples_per_s"],
            "speedup_ess": res["learned"]["ess_per_s"] / max(res["plain"]["ess_per_s"], 1e-30),
-           "validation_nll": {"plain_proposal": nll_plain, "learned": nll_learned}, "k_cap": k_cap,
+           "validation_nll": {"plain_proposal": nll_plain, "learned": nll_learned},
+           "importance_weighted": {"pairs": int(X.shape[0]), "weight_ess": ess_is, "scoring_s": t_is,
+                                   "weighted_validation_nll": {"plain_proposal": nll_is0, "learned_is": nll_is},
+                                   "race": res["learned_is"],
+                                   "speedup_accepted": res["learned_is"]["accepted_samples_per_s"] /
+                                                       res["plain"]["accepted_samples_per_s"]},
+           "k_cap": k_cap,
            "mean_clicks": float(marg60.sum()),
            "config": {"workload": f"M=60 synthetic lossy GBS state (r~U[0.5,1.0], eta=0.5, seed 6), {C} "
                                   "independence-MH chains targeting p(S | k <= k_cap); MADE 60-256-256-256-60 started at the "
                                   "plain proposal, trained (3000 Adam steps, batch 4096, best of held-out NLL) on "
-                                  "50 x C states of the plain exact chain"}}
+                                  "50 x C states of the plain exact chain ('learned'), or on 48 x C proposals "
+                                  "of the plain proposal scored by the exact kernel with self-normalised "
+                                  "weights p/q ('learned_is')"}}
     # M = 20: all 2^20 exact probabilities, then TV of the pooled chain states
     progress("M=20 exact table")
     st20 = gi.lossy_gbs_state(20, 0.5, 1.0, 0.5, 5)
@@ -459,19 +511,29 @@ def run_mh(args):
     net20 = tor.MLP(ctx, 20, 256, seed=5)
     net20.set_marginals(marginals(st20))
     train(net20, P20, torch.tensor(np.maximum(p20, 0), dtype=torch.float32, device="cuda"), 1500, 8192, 1e-3)
-    tv = {}
+    tv, curve = {}, {}
     C20 = 16 * C
+    checkpoints = (10, 25, 50, 100)
     for name, prop in (("plain", None), ("learned", net20)):
         progress(f"M=20 chains: {name}")
         chn = chains(st20, C20)
         run(chn, 20, 9, prop)
-        series = []
-        run(chn, 100, 9, prop, record=series, t0=20)
-        codes = np.concatenate([p[:, 0].cpu().numpy() for p in series])
-        freq = np.bincount(codes, minlength=1 << 20) / codes.size
-        tv[name] = 0.5 * float(np.abs(freq - p20).sum())
-    out["m20"] = {"tv_pooled_100_steps": tv, "chains": C20, "samples_pooled": 100 * C20, "exact_table_s": t_exact,
-                  "sum_p": float(p20.sum()), "subset_dets": 3 ** 20,
+        series, pts, el = [], [], 0.0
+        done = 0
+        for cp in checkpoints:              # time only the steps; TV of all states pooled so far
+            torch.cuda.synchronize()
+            t0s = time.perf_counter()
+            run(chn, cp - done, 9, prop, record=series, t0=20 + done)
+            torch.cuda.synchronize()
+            el += time.perf_counter() - t0s
+            done = cp
+            codes = np.concatenate([p[:, 0].cpu().numpy() for p in series])
+            freq = np.bincount(codes, minlength=1 << 20) / codes.size
+            pts.append({"steps": cp, "s": el, "tv": 0.5 * float(np.abs(freq - p20).sum())})
+        tv[name] = pts[-1]["tv"]
+        curve[name] = pts
+    out["m20"] = {"tv_pooled_100_steps": tv, "tv_vs_time": curve, "chains": C20, "samples_pooled": 100 * C20,
+                  "exact_table_s": t_exact, "sum_p": float(p20.sum()), "subset_dets": 3 ** 20,
                   "statuses_ok": int((r20["status"] == 0).sum())}
     print(json.dumps(out), flush=True)
     ctx.close()
