@@ -273,6 +273,84 @@ def run_adaptive(args):
     ctx.close()
 
 
+def run_table(args):
+    """Every click pattern's Torontonian of one M-mode state (tor_all_patterns): one walk over
+    the 2^M subsets and a Moebius transform, against the patterns one by one."""
+    import math
+    import torch
+    from paper_2009_01177_gb300 import gbs_inputs as gi
+    from paper_2009_01177_gb300 import tor
+    ctx = tor.Context(0)
+    M = args.table_m
+    st = gi.lossy_gbs_state(M, 0.5, 1.0, 0.5, 5)
+    Od = torch.from_numpy(st.O).cuda()
+    s_, ld_ = np.linalg.slogdet(np.eye(2 * M) - st.O)
+    prec = "fx128" if -0.5 * ld_ / math.log(2) <= 11 else "dd"
+    n = 1 << M
+    out = torch.zeros(n * tor.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        ctx.all_patterns_async(Od, out, prec=prec)
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    walk_ms, tr_ms = [], []
+    with ClockSampler(0) as clocks:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            ev[i][0].record()
+            ctx.all_patterns_async(Od, out, prec=prec)
+            ev[i][1].record()
+            walk_ms.append(ctx.walk_time_ms())
+            tr_ms.append(ctx.transform_time_ms())
+        torch.cuda.synchronize()
+    ctx.set_timing(False)
+    step_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    walk = float(np.mean(walk_ms))
+    tr = float(np.mean(tr_ms))
+    # transform traffic per entry: the first pass reads the 32-byte term and writes it and its
+    # 8-byte sum; every later pass reads and writes both; passes of 10 bits, then 5, the last shorter
+    passes, b = 0, 0
+    while b < M:
+        b += 10 if b == 0 else 5
+        passes += 1
+    tr_bytes = n * (72 + (passes - 1) * 80) if M >= 10 else None
+    # the patterns one by one (tor_batch_patterns), timed on a uniform sample and scaled to 2^M
+    rng = np.random.default_rng(5)
+    sample = (rng.random((4096, M)) < 0.5).astype(np.uint8)
+    P = tor.pack_patterns(sample, M).cuda()
+    ob = torch.zeros(4096 * tor.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    ctx.batch_patterns_async(Od, P, ob, prec=prec)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ctx.batch_patterns_async(Od, P, ob, prec=prec)
+    e1.record()
+    torch.cuda.synchronize()
+    per_pattern_s = e0.elapsed_time(e1) * 1e-3 / 4096
+    r = tor.results_array(out, n)
+    scale = math.exp(-0.5 * float(np.linalg.slogdet(st.Sigma)[1]))
+    line = {"metric": f"all 2^{M} click-pattern Torontonians of one state", "value": n / (step_ms * 1e-3),
+            "unit": "Tor/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+            "higher_is_better": True, "dtype": prec, "data": "synthetic",
+            "config": {"workload": f"M={M} synthetic lossy GBS state (r~U[0.5,1.0], Haar U, eta=0.5, seed 5); "
+                                   f"tor_all_patterns: walk over 2^{M} subsets, Moebius transform of the exact "
+                                   "term table", "l2": f"table of {n * 40 / 2**30:.2f} GiB, far above L2"},
+            "walk_ms": walk, "walk_subset_dets_per_s": n / (walk * 1e-3), "transform_ms": tr,
+            "roofline": {"bound": "hbm", "kernel": "k_mobius_pass (+ sums init)",
+                         "achieved": tr_bytes / (tr * 1e-3) / 1e9 if tr_bytes else None,
+                         "peak": 6767.7, "unit": "GB/s",
+                         "frac": tr_bytes / (tr * 1e-3) / 1e9 / 6767.7 if tr_bytes else None,
+                         "traffic": None, "passes": passes,
+                         "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+            "one_by_one": {"s_per_pattern": per_pattern_s, "projected_s": per_pattern_s * n,
+                           "speedup": per_pattern_s * n / (step_ms * 1e-3),
+                           "sample": "4096 uniform random patterns through tor_batch_patterns, same tier"},
+            "sum_p": float((r["hi"] + r["lo"]).sum()) * scale, "statuses_ok": int((r["status"] == 0).sum()),
+            "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_batch(args):
     """Batched Tor/s for 4096 patterns (k in [8, 30]) against one launch per pattern."""
     import torch
@@ -499,11 +577,12 @@ def run_mh(args):
     allx = ((np.arange(1 << 20)[:, None] >> np.arange(20)[None, :]) & 1).astype(np.uint8)
     O20 = torch.from_numpy(st20.O).cuda()
     P20 = tor.pack_patterns(allx, 20).cuda()
+    # every pattern's exact probability from one walk over the 2^20 subsets (tor_all_patterns)
     o20 = torch.zeros((1 << 20) * tor.RESULT_BYTES, dtype=torch.uint8, device="cuda")
-    ctx.batch_patterns_async(O20, P20, o20, prec="auto", tol=1e-6)
+    ctx.all_patterns_async(O20, o20, prec="fx128")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ctx.batch_patterns_async(O20, P20, o20, prec="auto", tol=1e-6)
+    ctx.all_patterns_async(O20, o20, prec="fx128")
     torch.cuda.synchronize()
     t_exact = time.perf_counter() - t0
     r20 = tor.results_array(o20, 1 << 20)
@@ -533,7 +612,8 @@ def run_mh(args):
         tv[name] = pts[-1]["tv"]
         curve[name] = pts
     out["m20"] = {"tv_pooled_100_steps": tv, "tv_vs_time": curve, "chains": C20, "samples_pooled": 100 * C20,
-                  "exact_table_s": t_exact, "sum_p": float(p20.sum()), "subset_dets": 3 ** 20,
+                  "exact_table_s": t_exact, "exact_table": "tor_all_patterns, 128-bit fixed point",
+                  "sum_p": float(p20.sum()), "subset_dets": 2 ** 20,
                   "statuses_ok": int((r20["status"] == 0).sum())}
     print(json.dumps(out), flush=True)
     ctx.close()
@@ -548,7 +628,8 @@ def main():
     ap.add_argument("--k", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--mode", default="single", choices=["single", "batch", "mh", "adaptive"])
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "mh", "adaptive", "table"])
+    ap.add_argument("--table-m", type=int, default=26, help="table mode: modes M (2^M patterns)")
     ap.add_argument("--n", type=int, default=4096, help="patterns (batch) or chains (mh)")
     ap.add_argument("--chunk-bits", type=int, default=None,
                     help="single mode: chunk depth d instead of the autotuner's choice")
@@ -568,6 +649,9 @@ def main():
         return
     if args.mode == "adaptive":
         run_adaptive(args)
+        return
+    if args.mode == "table":
+        run_table(args)
         return
 
     import torch

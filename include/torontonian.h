@@ -190,6 +190,29 @@ int tor_chunks(tor_ctx *ctx, const double *O, int k, int ld, int layout, int pre
 int tor_single_noalloc(const double *O, int k, int ld, int layout, int prec,
                        cudaStream_t stream, tor_result *out_dev);
 
+/*
+ * tor_all_patterns: Tor(O_S) for EVERY click pattern S of one M-mode state.
+ * For the full matrix, (O_S)_Z = O_Z (the selection rule of Eq. 1 applied
+ * twice), so the terms t_Z = 1/sqrt(det(I - O_Z)) of Eq. 2 are shared by all
+ * patterns and Tor(O_S) = sum over Z inside S of (-1)^(|S|-|Z|) t_Z is the
+ * Moebius transform of the t table: one walk over the 2^M subsets stores
+ * every t_Z exactly (256-bit fixed point, 128 fraction bits), and an integer
+ * transform turns the table into all 2^M Torontonians.  2^M determinants
+ * instead of 3^M; each result has the same error model as tor_single.
+ *   O       dev  2M x 2M FP64 O = I - Sigma^-1, xxpp order, leading dim ld.
+ *   prec    TOR_PREC_FP64, TOR_PREC_DD or TOR_PREC_FX128 (the state's
+ *           t_max <= 2^11 is checked for the latter).
+ *   out_dev dev  2^M results; entry S (bit j = mode j clicked) holds
+ *           Tor(O_S), so p(S) = Tor(O_S) / sqrt(det Sigma).  A status bit
+ *           raised by any subset (not positive definite) marks every entry.
+ * Workspace: 40 bytes per pattern (M = 30: 43 GB) plus the walk's stacks.
+ * Asynchronous on `stream` (it synchronises once when the walk-order table
+ * is first made).  M in [1, TOR_TABLE_MAX_M].
+ */
+#define TOR_TABLE_MAX_M 30
+int tor_all_patterns(tor_ctx *ctx, const double *O, int M, int ld, int prec, cudaStream_t stream,
+                     tor_result *out_dev);
+
 /* tor_fx256_mul: n elementwise products of 256-bit fixed-point numbers exactly
  * as the TOR_PREC_FX256 tier forms them (Sec. 5.1-5.3: magnitudes multiplied,
  * truncated to 192 fraction bits, sign restored), so that the arithmetic can
@@ -352,6 +375,11 @@ int tor_set_timing(tor_ctx *ctx, int on);
 /* Duration in ms of the walk kernel of the most recent timed call (waits for
  * that kernel to finish).  TOR_EINVAL if no timed call was made. */
 int tor_walk_time(tor_ctx *ctx, float *ms);
+
+/* Duration in ms of the transform passes (sums of terms, then the Moebius
+ * transform over all mask bits) of the most recent timed tor_all_patterns
+ * call.  TOR_EINVAL if there was none. */
+int tor_transform_time(tor_ctx *ctx, float *ms);
 
 /*
  * tor_autotune: pick the chunk depth d (walked modes per chunk k - d) and

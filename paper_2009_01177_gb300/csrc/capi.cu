@@ -7,6 +7,7 @@
 #include <new>
 #include <cstdlib>
 #include <cmath>
+#include <vector>
 #include "tor_internal.h"
 #include "tor_walk.cuh"
 
@@ -49,8 +50,8 @@ struct tor_ctx {
   int blocks_per_sm = 4;  // clamped to the kernel's occupancy at launch
   int chunk_bits = -1;  // -1: automatic
   Buf B, Blo, scratch, block_part, status, result, total8, bound;
-  bool timing = false, timed = false;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timing = false, timed = false, transform_timed = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
   // batch workspace (tor_batch_reserve)
   int batch_nmax = 0, batch_kmax = -1;
   bool batch_explicit = false;  // sized by the caller's tor_batch_reserve: never re-read k
@@ -60,6 +61,8 @@ struct tor_ctx {
   unsigned char *r1_table_dev = nullptr;
   int *k_dev = nullptr;  // pattern mode: click counts
   Buf mh;                // sampler: proposals, their log q, their Torontonians
+  Buf table, table_s, order;  // all-pattern table: exact terms, sums of terms, walk order
+  int order_r1 = -1;          // walked modes the order table was made for
   unsigned char r1_table[5][65];  // walked modes per chunk, by tier (TOR_PREC_*) and k
   // autotuned single-instance settings by tier and k (-1: not tuned)
   signed char tuned_d[5][65];   // by tier (TOR_PREC_FP64 .. TOR_PREC_FX256) and k
@@ -228,11 +231,13 @@ void tor_destroy(tor_ctx *c) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   Buf *bufs[] = {&c->B, &c->Blo, &c->scratch, &c->block_part, &c->status, &c->result, &c->total8, &c->bound,
-                 &c->batch, &c->batch_scratch, &c->mh};
+                 &c->batch, &c->batch_scratch, &c->mh, &c->table, &c->table_s, &c->order};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->ev2) cudaEventDestroy(c->ev2);
+  if (c->ev3) cudaEventDestroy(c->ev3);
   delete c;
 }
 
@@ -242,9 +247,20 @@ int tor_set_timing(tor_ctx *ctx, int on) {
   if (on && !ctx->ev0) {
     CK(cudaEventCreate(&ctx->ev0));
     CK(cudaEventCreate(&ctx->ev1));
+    CK(cudaEventCreate(&ctx->ev2));
+    CK(cudaEventCreate(&ctx->ev3));
   }
   ctx->timing = on != 0;
   ctx->timed = false;
+  ctx->transform_timed = false;
+  return TOR_OK;
+}
+
+int tor_transform_time(tor_ctx *ctx, float *ms) {
+  if (!ctx || !ms) return fail(TOR_EINVAL, "null pointer");
+  if (!ctx->transform_timed) return fail(TOR_EINVAL, "no timed tor_all_patterns call since timing was enabled");
+  CK(cudaEventSynchronize(ctx->ev3));
+  CK(cudaEventElapsedTime(ms, ctx->ev2, ctx->ev3));
   return TOR_OK;
 }
 
@@ -399,6 +415,92 @@ int tor_fx256_mul(const uint64_t *a_dev, const uint64_t *b_dev, int n, uint64_t 
   if (tor::launch_fx256_mul((const unsigned long long *)a_dev, (const unsigned long long *)b_dev, n,
                             (unsigned long long *)out_dev, ovf_dev, stream))
     return fail(TOR_ECUDA, "launch: %s", cudaGetErrorString(cudaGetLastError()));
+  return TOR_OK;
+}
+
+// low-mode masks of a chunk's terms in the order the walk visits them: the
+// chunk root (no low mode) first, then depth first, a node's children pivoting
+// on its remaining modes from the highest down, each child's own term before
+// its subtree, a child keeping the modes above its pivot
+static void walk_order(unsigned int mask, int q, int r1, std::vector<unsigned int> &seq) {
+  for (int cur = 0; cur < r1 - q; ++cur) {
+    const int p = r1 - 1 - cur;
+    const unsigned int m2 = mask | (1u << p);
+    seq.push_back(m2);
+    walk_order(m2, p + 1, r1, seq);
+  }
+}
+
+int tor_all_patterns(tor_ctx *ctx, const double *O, int M, int ld, int prec, cudaStream_t s, tor_result *out_dev) {
+  if (!ctx) return fail(TOR_EINVAL, "null context");
+  if (M < 1 || M > TOR_TABLE_MAX_M) return fail(TOR_EINVAL, "M = %d outside [1, %d]", M, TOR_TABLE_MAX_M);
+  if (!O || !out_dev) return fail(TOR_EINVAL, "null pointer");
+  if (ld < 2 * M) return fail(TOR_EINVAL, "ld = %d < 2M = %d", ld, 2 * M);
+  if (prec != TOR_PREC_FP64 && prec != TOR_PREC_DD && prec != TOR_PREC_FX128)
+    return fail(TOR_EINVAL, "prec must be TOR_PREC_FP64, TOR_PREC_DD or TOR_PREC_FX128");
+  CK(cudaSetDevice(ctx->device));
+  int rc;
+  const int k = M;
+  if (prec == TOR_PREC_FX128) {  // every subset's t_max is at most the full state's
+    if ((rc = ensure(ctx, ctx->bound, sizeof(tor_bound)))) return rc;
+    if (tor::launch_bounds_single(O, k, ld, TOR_LAYOUT_XXPP, 1e-10, (tor_bound *)ctx->bound.p, s))
+      return fail(TOR_ECUDA, "bound pass launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    tor_bound bd;
+    CK(cudaMemcpyAsync(&bd, ctx->bound.p, sizeof(bd), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!(bd.log_tmax <= tor::FX128_MAX_LOG2_TMAX * 0.6931472f))
+      return fail(TOR_EINVAL, "state outside the 128-bit fixed-point range (log2 t_max = %.2f)",
+                  (double)bd.log_tmax / 0.6931472);
+  }
+  // walked modes per chunk: at least 2^16 chunks to fill the grid, at most 12
+  // modes (a 4096-entry walk-order table)
+  int r1 = k - 16;
+  if (r1 > 12) r1 = 12;
+  if (r1 < 0) r1 = 0;
+  const int block = ctx->threads_per_block;
+  const int occ = tor::table_walk_max_blocks_per_sm(prec, block);
+  const int grid = ctx->sms * (ctx->blocks_per_sm < occ ? ctx->blocks_per_sm : occ);
+  const size_t nthreads = (size_t)grid * block;
+  const size_t n = (size_t)1 << M;
+  if ((rc = ensure(ctx, ctx->B, sizeof(double) * 4 * (size_t)k * k))) return rc;
+  if ((rc = ensure(ctx, ctx->Blo, sizeof(double) * 2 * (size_t)k))) return rc;
+  if ((rc = ensure(ctx, ctx->scratch, sizeof(double) * nthreads * (size_t)tor::scratch_entries(prec, k, r1)))) return rc;
+  if ((rc = ensure(ctx, ctx->status, sizeof(int)))) return rc;
+  if ((rc = ensure(ctx, ctx->table, sizeof(tor::Fx256) * n))) return rc;
+  if ((rc = ensure(ctx, ctx->table_s, sizeof(double) * n))) return rc;
+  if ((rc = ensure(ctx, ctx->order, sizeof(unsigned int) << r1))) return rc;
+  if (ctx->order_r1 != r1) {
+    std::vector<unsigned int> seq;
+    seq.reserve((size_t)1 << r1);
+    seq.push_back(0u);
+    walk_order(0u, 0, r1, seq);
+    if (seq.size() != ((size_t)1 << r1)) return fail(TOR_ECUDA, "walk order of %zu entries", seq.size());
+    CK(cudaMemcpyAsync(ctx->order.p, seq.data(), sizeof(unsigned int) << r1, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));  // seq is a local
+    ctx->order_r1 = r1;
+  }
+  tor::launch_prep(O, k, ld, TOR_LAYOUT_XXPP, (double *)ctx->B.p, (double *)ctx->Blo.p, s);
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(ctx->status.p, 0, sizeof(int), s));
+  if (ctx->timing) CK(cudaEventRecord(ctx->ev0, s));
+  if (tor::launch_table_walk(prec, grid, block, (const double *)ctx->B.p, (const double *)ctx->Blo.p, k, r1,
+                             (double *)ctx->scratch.p, (const unsigned int *)ctx->order.p,
+                             (tor::Fx256 *)ctx->table.p, (int *)ctx->status.p, s))
+    return fail(TOR_ECUDA, "table walk: %s", cudaGetErrorString(cudaGetLastError()));
+  if (ctx->timing) {
+    CK(cudaEventRecord(ctx->ev1, s));
+    ctx->timed = true;
+  }
+  if (ctx->timing) CK(cudaEventRecord(ctx->ev2, s));
+  if (tor::launch_table_transform((tor::Fx256 *)ctx->table.p, (double *)ctx->table_s.p, M, s))
+    return fail(TOR_ECUDA, "table transform: %s", cudaGetErrorString(cudaGetLastError()));
+  if (ctx->timing) {
+    CK(cudaEventRecord(ctx->ev3, s));
+    ctx->transform_timed = true;
+  }
+  if (tor::launch_table_finalize((const tor::Fx256 *)ctx->table.p, (const double *)ctx->table_s.p, M, prec,
+                                 (const int *)ctx->status.p, out_dev, s))
+    return fail(TOR_ECUDA, "table finalize: %s", cudaGetErrorString(cudaGetLastError()));
   return TOR_OK;
 }
 

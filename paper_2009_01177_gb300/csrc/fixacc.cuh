@@ -22,7 +22,7 @@
 namespace tor {
 
 template <int L>
-struct FxW {
+struct alignas(16) FxW {
   unsigned long long w[L];  // little-endian limbs, value = signed int / 2^(32 L)
 };
 using Fx256 = FxW<4>;  // 128 fraction bits

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include "../../include/torontonian.h"
+#include "fixacc.cuh"
 
 namespace tor {
 
@@ -82,6 +83,13 @@ void launch_dfs(int tier, int grid, int block, const double *B, const double *Bl
 void launch_finalize(const unsigned long long *block_part, int nblocks, int k, int tier,
                      const int *status, tor_result *out, cudaStream_t s);
 void launch_dfma_peak(double *sink, int grid, int block, int iters, cudaStream_t s);
+// all-pattern tables (tor_table.cu)
+int table_walk_max_blocks_per_sm(int tier, int block);
+int launch_table_walk(int tier, int grid, int block, const double *B, const double *Blo, int k, int r1,
+                      double *scratch, const unsigned int *order, Fx256 *table, int *status, cudaStream_t s);
+int launch_table_transform(Fx256 *t, double *s, int M, cudaStream_t st);
+int launch_table_finalize(const Fx256 *t, const double *s, int M, int tier, const int *status, tor_result *out,
+                          cudaStream_t st);
 int launch_fx256_mul(const unsigned long long *a, const unsigned long long *b, int n, unsigned long long *out,
                      int *ovf, cudaStream_t s);
 int scratch_entries(int tier, int k, int r1);

@@ -92,6 +92,7 @@ SIGNATURES = {
     "tor_chunks": (_I, [_VP, _VP, _I, _I, _I, _I, _I, _U64, _U64, _VP, _VP]),
     "tor_fixed_to_result": (_I, [ctypes.POINTER(_U64), _I, _I, ctypes.POINTER(TorResultC)]),
     "tor_fx256_mul": (_I, [_VP, _VP, _I, _VP, _VP, _VP]),
+    "tor_all_patterns": (_I, [_VP, _VP, _I, _I, _I, _VP, _VP]),
     "tor_batch": (_I, [_VP, _VP, _VP, _VP, _I, _I, _I, _D, _VP, _VP]),
     "tor_bounds": (_I, [_VP, _VP, _VP, _VP, _I, _I, _D, _VP, _VP]),
     "tor_batch_reserve": (_I, [_VP, _I, _I]),
@@ -114,6 +115,7 @@ SIGNATURES = {
     "tor_autotune": (_I, [_VP, _I, _I, ctypes.c_char_p, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "tor_set_timing": (_I, [_VP, _I]),
     "tor_walk_time": (_I, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "tor_transform_time": (_I, [_VP, ctypes.POINTER(ctypes.c_float)]),
 }
 
 
@@ -238,6 +240,21 @@ class Context:
                                    chunk_bits, c_begin, c_end, _stream(stream), part.data_ptr()))
         return part
 
+    def all_patterns_async(self, Ofull: torch.Tensor, out: torch.Tensor, prec: str = "fp64", stream=None):
+        """tor_all_patterns: out is a uint8 CUDA tensor of 2^M * RESULT_BYTES."""
+        M, ld = _mat(Ofull)
+        if out.numel() < (1 << M) * RESULT_BYTES:
+            raise ValueError("out too small")
+        _check(self.lib.tor_all_patterns(self.h, Ofull.data_ptr(), M, ld, _PREC[prec], _stream(stream),
+                                         out.data_ptr()))
+
+    def all_patterns(self, Ofull: torch.Tensor, prec: str = "fp64"):
+        """Tor(O_S) of every pattern S of the M-mode state (index = mask); a numpy structured array."""
+        M = Ofull.shape[0] // 2
+        out = torch.zeros((1 << M) * RESULT_BYTES, dtype=torch.uint8, device=Ofull.device)
+        self.all_patterns_async(Ofull, out, prec=prec)
+        return results_array(out, 1 << M)
+
     def bounds(self, Os, tol: float = 1e-10, layout: str = "xxpp", stream=None):
         """FP32 bound pass for a list of 2k x 2k float64 CUDA tensors; returns a list of dicts."""
         n = len(Os)
@@ -325,6 +342,11 @@ class Context:
 
     def set_timing(self, on: bool):
         _check(self.lib.tor_set_timing(self.h, int(bool(on))))
+
+    def transform_time_ms(self) -> float:
+        ms = ctypes.c_float()
+        _check(self.lib.tor_transform_time(self.h, ctypes.byref(ms)))
+        return ms.value
 
     def walk_time_ms(self) -> float:
         ms = ctypes.c_float()
