@@ -456,3 +456,24 @@ def test_fx256_rejects_out_of_range(ctx, cuda_lib):
     assert ei.value.code == cuda_lib.TOR_EINVAL
     with pytest.raises(cuda_lib.TorError):
         ctx.batch([dev(gi.thermal_O(3, 0.25))], prec="fx256")     # batches have no 256-bit tier
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fx256"])
+def test_long_run_cancel_and_resume(ctx, prec, tmp_path):
+    # windows of tor_chunks with a checkpoint: stopped after three windows, resumed, and
+    # bit-identical to the partials summed in one go
+    from paper_2009_01177_gb300 import longrun, shard
+    from paper_2009_01177_gb300.tor import fixed_to_result
+    st_, pat, O32 = gi.workload_m100(32)
+    k, d, window = 20, 12, 512
+    Od = dev(gi.select(st_.O, pat[:k]))
+    ck = str(tmp_path / "long.npz")
+    stops = iter([False, False, False, True])
+    r0, s0 = longrun.tor_long(ctx, Od, prec, d, window, ck, should_stop=lambda: next(stops, True))
+    assert r0 is None and s0.done.sum() == 3
+    r1, s1 = longrun.tor_long(ctx, Od, prec, d, window, ck)
+    assert s1.complete
+    whole = shard.sum_partials(ctx.chunks(Od, d, 0, 1 << d, prec=prec).cpu().numpy().view(np.uint64))
+    assert np.array_equal(s1.total, whole)
+    ref = fixed_to_result([int(x) for x in whole], k, prec)
+    assert (r1.hi, r1.lo, r1.sum_abs) == (ref.hi, ref.lo, ref.sum_abs)
