@@ -104,10 +104,18 @@ __device__ __forceinline__ void fx_add_signed(Fx256 &acc, double x, bool neg, in
 #define TOR_F64_RSMEM 5
 #endif
 #ifndef TOR_DD_RSMEM
-#define TOR_DD_RSMEM 4
+#define TOR_DD_RSMEM 3
 #endif
 #ifndef TOR_F64_MINB
 #define TOR_F64_MINB 1
+#endif
+// double-double: one-mode register subtrees and three resident blocks (168
+// registers) beat two-mode subtrees at two blocks (186) by 23-29 % at k = 28-30
+#ifndef TOR_DD_MINB
+#define TOR_DD_MINB 3
+#endif
+#ifndef TOR_DD_RREG
+#define TOR_DD_RREG 1
 #endif
 // The fixed-point tier: 128-bit products are register-hungry (254 registers
 // with two-mode register subtrees, so two resident blocks), so its register
@@ -243,10 +251,10 @@ struct TierF64 {
 struct TierDD {
   using T = dd;
   static constexpr int W = 2;
-  static constexpr int RREG = 2;
+  static constexpr int RREG = TOR_DD_RREG;
   static constexpr int RUNROLL = 4;
   static constexpr int RSMEM = TOR_DD_RSMEM;
-  static constexpr int MINB = 1;
+  static constexpr int MINB = TOR_DD_MINB;
   static constexpr int PREC = 2;  // TOR_PREC_DD
   using Acc = Fx256;
 
