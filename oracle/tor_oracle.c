@@ -241,9 +241,12 @@ static int det_I_minus_OZ(const double *O, int k, int ld, const int *idx, int m,
  */
 static int tor_range_fx(const double *O, int k, int ld, int F, int nthreads, int mutation,
                         uint64_t mask_lo, uint64_t mask_hi, fx *tor_out, fx *sabs_out) {
-    if (k < 0 || k > 40 || ld < 2 * k || F < 64 || F > 240) return ORC_EINVAL;
-    uint64_t nmask = 1ull << k;
-    if (mask_hi > nmask) mask_hi = nmask;
+    /* ranges of masks work up to k = 64 (the whole sum is limited to k <= 40 below) */
+    if (k < 0 || k > 64 || ld < 2 * k || F < 64 || F > 240) return ORC_EINVAL;
+    if (k < 64 && mask_hi > (1ull << k)) mask_hi = 1ull << k;
+    if (mask_lo > mask_hi) mask_lo = mask_hi;
+    const long long count = (long long)(mask_hi - mask_lo);
+    if (count < 0) return ORC_EINVAL; /* more than 2^63 masks */
     int status = ORC_OK;
     fx tor = {{0, 0, 0, 0}}, sabs = {{0, 0, 0, 0}};
 #ifdef _OPENMP
@@ -259,9 +262,9 @@ static int tor_range_fx(const double *O, int k, int ld, int F, int nthreads, int
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 64)
 #endif
-        for (long long mm = (long long)mask_lo; mm < (long long)mask_hi; ++mm) {
+        for (long long mm = 0; mm < count; ++mm) {
             if (err) continue;
-            uint64_t mask = (uint64_t)mm;
+            uint64_t mask = mask_lo + (uint64_t)mm;
             int m = 0;
             for (int j = 0; j < k; ++j) if (mask >> j & 1) idx[m++] = j;
             if (mutation == 1 && m == 0) continue;                 /* mutation 1: drop Z = {} */

@@ -396,7 +396,7 @@ int tor_chunks(tor_ctx *ctx, const double *O, int k, int ld, int layout, int pre
   if (rc) return rc;
   if (k == 0) return fail(TOR_EINVAL, "tor_chunks needs k >= 1");
   if (prec < TOR_PREC_FP64 || prec > TOR_PREC_FX256) return fail(TOR_EINVAL, "prec must be an explicit tier");
-  if (chunk_bits < 0 || chunk_bits > k || chunk_bits > 40) return fail(TOR_EINVAL, "chunk_bits outside [0, min(k, 40)]");
+  if (chunk_bits < 0 || chunk_bits > k || chunk_bits > 63) return fail(TOR_EINVAL, "chunk_bits outside [0, min(k, 63)]");
   if (!part_dev) return fail(TOR_EINVAL, "null partials pointer");
   const uint64_t nchunks = 1ull << chunk_bits;
   if (c_begin > c_end || c_end > nchunks) return fail(TOR_EINVAL, "chunk range [%llu, %llu) outside [0, %llu)",

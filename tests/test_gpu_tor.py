@@ -477,3 +477,31 @@ def test_long_run_cancel_and_resume(ctx, prec, tmp_path):
     assert np.array_equal(s1.total, whole)
     ref = fixed_to_result([int(x) for x in whole], k, prec)
     assert (r1.hi, r1.lo, r1.sum_abs) == (ref.hi, ref.lo, ref.sum_abs)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fx256"])
+def test_maximum_k_sampled_chunk(ctx, prec):
+    # k = 64 (TOR_MAX_K, a 128 x 128 matrix): one chunk of 4096 subsets at d = 52 whose six
+    # fixed modes in Z include the highest one (masks above 2^63), against the oracle's exact range
+    from paper_2009_01177_gb300.tor import limbs_to_int
+    st, pat, O = gi.workload_m100(64)
+    k, d = 64, 52
+    c = (1 << 51) | (1 << 30) | 0xF
+    ref_t, ref_s = oracle.tor_exact(O, c << (k - d), (c + 1) << (k - d))
+    part = ctx.chunks(dev(O), d, c, c + 1, prec=prec).cpu().numpy()[0]
+    L = part.size // 2
+    got = Fraction(limbs_to_int(part[:L]), 1 << (32 * L))
+    sabs = Fraction(limbs_to_int(part[L:]), 1 << (32 * L))
+    u = {"fp64": 2.0 ** -53, "fx256": 2.0 ** -186}[prec]
+    assert abs(sabs - ref_s) <= Fraction(1e-12) * ref_s
+    assert abs(got - ref_t) <= 4 * k * Fraction(u) * ref_s + ref_s * Fraction(1, 2 ** 190)
+
+
+def test_chunk_depth_above_the_old_limit_and_k_limits(ctx, cuda_lib):
+    st, pat, O = gi.workload_m100(64)
+    Od = dev(O)
+    ctx.chunks(Od, 63, 5, 6)                         # d = 63: a chunk of two subsets
+    with pytest.raises(cuda_lib.TorError):
+        ctx.chunks(Od, 64, 0, 1)                     # d = k = 64 is beyond 63
+    with pytest.raises(cuda_lib.TorError):
+        ctx.single(dev(np.zeros((130, 130))))        # k = 65 > TOR_MAX_K

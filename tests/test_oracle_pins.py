@@ -233,3 +233,15 @@ def test_exact_output_agrees_with_the_double_double_output():
     a = oracle.tor_exact(O, 0, 300)
     b = oracle.tor_exact(O, 300, 1 << 10)
     assert (a[0] + b[0], a[1] + b[1]) == (tor_x, sabs_x)
+
+
+def test_exact_output_mask_range_at_k64():
+    # the largest k, masks above 2^63: O = I/4 gives t_Z = (4/3)^|Z| with sign (-1)^(64-|Z|)
+    k = 64
+    lo = (1 << 63) | (0x5A << 40)
+    hi = lo + 4096
+    tor_x, sabs_x = oracle.tor_exact(gi.thermal_O(k, 0.25), lo, hi)
+    exact_t = sum((-1) ** (k - bin(m).count("1")) * Fraction(4, 3) ** bin(m).count("1") for m in range(lo, hi))
+    exact_s = sum(Fraction(4, 3) ** bin(m).count("1") for m in range(lo, hi))
+    assert abs(sabs_x - exact_s) <= Fraction(1, 2 ** 190) * exact_s
+    assert abs(tor_x - exact_t) <= Fraction(1, 2 ** 190) * exact_s
