@@ -106,8 +106,34 @@ k_mobius_pass(Fx256 *__restrict__ t, double *__restrict__ s, int M, int b, int n
     ts[e] = init_s ? fx_to_double(v) : s[m];
   }
   __syncthreads();
-  for (int j = 0; j < nb; ++j) {
-    // pairs (e, e + lo_n 2^j) with bit j of i clear
+  int j = 0;
+  // two bits at a time in registers: each thread takes the quad of entries that
+  // differ in bits j and j + 1 of i, and writes back the three that change
+  for (; j + 1 < nb; j += 2) {
+    for (int q = threadIdx.x; q < TILE / 4; q += MOB_THREADS) {
+      const int l = q % lo_n, r = q / lo_n;                          // r: i with bits j, j+1 removed
+      const int i0 = ((r >> j) << (j + 2)) | (r & ((1 << j) - 1));
+      const int e0 = i0 * lo_n + l, st = lo_n << j;
+      Fx256 v[4];
+      double sv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * st;
+        v[u].w[0] = tw[0][e]; v[u].w[1] = tw[1][e]; v[u].w[2] = tw[2][e]; v[u].w[3] = tw[3][e];
+        sv[u] = ts[e];
+      }
+      fx_sub(v[1], v[0]); fx_sub(v[3], v[2]); sv[1] += sv[0]; sv[3] += sv[2];   // bit j
+      fx_sub(v[2], v[0]); fx_sub(v[3], v[1]); sv[2] += sv[0]; sv[3] += sv[1];   // bit j + 1
+#pragma unroll
+      for (int u = 1; u < 4; ++u) {
+        const int e = e0 + u * st;
+        tw[0][e] = v[u].w[0]; tw[1][e] = v[u].w[1]; tw[2][e] = v[u].w[2]; tw[3][e] = v[u].w[3];
+        ts[e] = sv[u];
+      }
+    }
+    __syncthreads();
+  }
+  for (; j < nb; ++j) {  // an odd last bit: pairs (e, e + lo_n 2^j) with bit j of i clear
     for (int p = threadIdx.x; p < TILE / 2; p += MOB_THREADS) {
       const int l = p % lo_n, q = p / lo_n;                         // q: i with bit j removed
       const int i0 = ((q >> j) << (j + 1)) | (q & ((1 << j) - 1));
