@@ -146,7 +146,9 @@ int tor_single(tor_ctx *ctx, const double *O, int k, int ld, int layout, int pre
  * tor_single_async: as tor_single, but the result goes to device memory
  * `out_dev` and the call returns after enqueueing (capturable in a CUDA
  * graph once the workspace has been sized by an earlier call with the same
- * k and precision).  prec must be TOR_PREC_FP64 or TOR_PREC_DD.
+ * k and precision).  prec: an explicit tier (TOR_PREC_FP64, _DD, _FX128 or
+ * _FX256); the fixed-point range is not checked here (tor_single checks it),
+ * a product that leaves the range sets the result's status to TOR_EINVAL.
  */
 int tor_single_async(tor_ctx *ctx, const double *O, int k, int ld, int layout, int prec,
                      cudaStream_t stream, tor_result *out_dev);
@@ -155,9 +157,12 @@ int tor_single_async(tor_ctx *ctx, const double *O, int k, int ld, int layout, i
  * tor_chunks: partial sums over a range of prefix chunks, for sharding the
  * 2^k subsets across processes or calls, resuming long runs, and checking
  * sampled chunks against an independent evaluation.
- *   chunk_bits  d: chunk c covers the subset masks [c 2^(k-d), (c+1) 2^(k-d)),
- *               i.e. modes k-d..k-1 are fixed by the bits of c.
- *   c_begin, c_end  the chunk range [c_begin, c_end) to evaluate.
+ *   prec        an explicit tier (TOR_PREC_FP64, _DD, _FX128 or _FX256).
+ *   chunk_bits  d in [0, min(k, 63)]: chunk c covers the subset masks
+ *               [c 2^(k-d), (c+1) 2^(k-d)), i.e. modes k-d..k-1 are fixed by
+ *               the bits of c.  k >= 1.
+ *   c_begin, c_end  the chunk range [c_begin, c_end) to evaluate (TOR_EINVAL
+ *               beyond 2^d).  Asynchronous on `stream`.
  *   part_dev    dev, (c_end - c_begin) x 8 uint64: per chunk the exact sum of
  *               (-1)^(k-|Z|) t_Z and of t_Z, each a 256-bit two's-complement
  *               fixed-point number with 128 fractional bits, little-endian
