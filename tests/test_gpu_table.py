@@ -93,3 +93,44 @@ def test_table_argument_checks(ctx, cuda_lib):
     big = torch.zeros((62, 62), dtype=torch.float64, device="cuda")    # M = 31 > TOR_TABLE_MAX_M
     out = torch.zeros(64, dtype=torch.uint8, device="cuda")
     assert ctx.lib.tor_all_patterns(ctx.h, big.data_ptr(), 31, 62, 1, None, out.data_ptr()) == cuda_lib.TOR_EINVAL
+
+
+@pytest.mark.parametrize("M", [1, 9])
+def test_smallest_tables(ctx, M):
+    # M = 1 (two patterns) and M = 9 (the per-bit transform's largest size)
+    st = gi.lossy_gbs_state(M, 0.5, 1.0, 0.5, 56 + M)
+    Od = torch.from_numpy(st.O).cuda()
+    tab = ctx.all_patterns(Od, prec="dd")
+    assert (tab["hi"][0], tab["lo"][0]) == (1.0, 0.0)           # Tor of no clicks is 1
+    for S in range(1, 1 << M):
+        modes = [j for j in range(M) if S >> j & 1]
+        r = ctx.single(torch.from_numpy(gi.select(st.O, modes)).cuda(), prec="dd")
+        diff = abs((Fraction(tab["hi"][S]) + Fraction(tab["lo"][S])) - (Fraction(r.hi) + Fraction(r.lo)))
+        assert float(diff) <= tab["err_est"][S] + r.err_est, S
+
+
+def test_largest_table(ctx, cuda_lib):
+    # M = 30 (TOR_TABLE_MAX_M): 2^30 patterns, 43 GB of results; sampled entries and the total
+    M = 30
+    st = gi.lossy_gbs_state(M, 0.5, 1.0, 0.5, 60)
+    Od = torch.from_numpy(st.O).cuda()
+    n = 1 << M
+    out = torch.zeros(n * cuda_lib.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    ctx.all_patterns_async(Od, out, prec="fp64")
+    rec = out.view(n, cuda_lib.RESULT_BYTES)
+    hi = rec[:, 0:8].contiguous().view(torch.float64).view(-1)
+    lo = rec[:, 8:16].contiguous().view(torch.float64).view(-1)
+    status = rec[:, 36:40].contiguous().view(torch.int32).view(-1)
+    assert int((status != 0).sum()) == 0
+    total = float((hi.sum() + lo.sum()).item()) * math.exp(-0.5 * np.linalg.slogdet(st.Sigma)[1])
+    assert abs(total - 1.0) < 1e-9
+    rng = np.random.default_rng(60)
+    masks = [(1 << 29) | 3] + [int(x) & int(rng.integers(0, n)) for x in rng.integers(0, n, 6)]
+    got = cuda_lib.results_from_tensor(rec[torch.tensor(masks, device="cuda")].reshape(-1), len(masks))
+    for S, r in zip(masks, got):
+        modes = [j for j in range(M) if S >> j & 1]
+        s1 = ctx.single(torch.from_numpy(gi.select(st.O, modes)).cuda(), prec="fp64")
+        diff = abs((Fraction(r.hi) + Fraction(r.lo)) - (Fraction(s1.hi) + Fraction(s1.lo)))
+        assert float(diff) <= r.err_est + s1.err_est, S
+    del out, rec, hi, lo, status
+    torch.cuda.empty_cache()
