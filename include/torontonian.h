@@ -218,6 +218,36 @@ int tor_single_noalloc(const double *O, int k, int ld, int layout, int prec,
 int tor_all_patterns(tor_ctx *ctx, const double *O, int M, int ld, int prec, cudaStream_t stream,
                      tor_result *out_dev);
 
+/*
+ * tor_levels: Tor by the paper's own schedule, Algorithm 1 level by level
+ * (all Z with |Z| = m together, m = 0..k) with each level's C(k, m) masks
+ * shared out by Algorithm 2 (unranking, then the next mask of the same
+ * popcount), and a fresh elimination of B_Z = I - O_Z for every subset, summed
+ * exactly.  A second, independent GPU evaluation of Eq. 2 (another subset
+ * order, another factorization of every term) for cross-checks beyond the CPU
+ * oracle's reach; about k/3 times the work of tor_single's walk per subset.
+ *   O, k, ld, layout   as for tor_single; k in [0, 48].
+ *   prec        TOR_PREC_FP64, TOR_PREC_DD or TOR_PREC_FX128 for every level,
+ *   level_prec  host, k + 1 tiers for the levels m = 0..k (the paper's per-|Z|
+ *               precision choice), or NULL to use prec throughout.
+ *   workspace   dev, caller-owned, at least tor_levels_workspace() bytes.
+ *   out_dev     dev, one result; err_est adds 4k u(tier) sum t over the levels
+ *               and tier is the least precise tier used.
+ * Asynchronous on `stream` (no allocation); failures are described by
+ * tor_levels_last_error().
+ */
+int tor_levels_workspace(int k, int device, size_t *bytes);
+int tor_levels(const double *O, int k, int ld, int layout, int prec, const int *level_prec, void *workspace,
+               size_t workspace_bytes, cudaStream_t stream, tor_result *out_dev);
+const char *tor_levels_last_error(void);
+
+/* Algorithm 2's mask functions (host, no GPU).  tor_level_next_mask: the next
+ * smaller mask with the same popcount (the paper's example: 010011 -> 001110),
+ * 0 when none is left.  tor_level_kth_mask: the r-th (0-based) mask of
+ * popcount m over k bits in decreasing order; TOR_EINVAL for r >= C(k, m). */
+uint64_t tor_level_next_mask(uint64_t mask);
+int tor_level_kth_mask(int k, int m, uint64_t r, uint64_t *mask);
+
 /* tor_fx256_mul: n elementwise products of 256-bit fixed-point numbers exactly
  * as the TOR_PREC_FX256 tier forms them (Sec. 5.1-5.3: magnitudes multiplied,
  * truncated to 192 fraction bits, sign restored), so that the arithmetic can

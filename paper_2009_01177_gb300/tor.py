@@ -92,6 +92,11 @@ SIGNATURES = {
     "tor_chunks": (_I, [_VP, _VP, _I, _I, _I, _I, _I, _U64, _U64, _VP, _VP]),
     "tor_fixed_to_result": (_I, [ctypes.POINTER(_U64), _I, _I, ctypes.POINTER(TorResultC)]),
     "tor_fx256_mul": (_I, [_VP, _VP, _I, _VP, _VP, _VP]),
+    "tor_levels_workspace": (_I, [_I, _I, ctypes.POINTER(ctypes.c_size_t)]),
+    "tor_levels": (_I, [_VP, _I, _I, _I, _I, ctypes.POINTER(_I), _VP, ctypes.c_size_t, _VP, _VP]),
+    "tor_levels_last_error": (ctypes.c_char_p, []),
+    "tor_level_next_mask": (_U64, [_U64]),
+    "tor_level_kth_mask": (_I, [_I, _I, _U64, ctypes.POINTER(_U64)]),
     "tor_all_patterns": (_I, [_VP, _VP, _I, _I, _I, _VP, _VP]),
     "tor_batch": (_I, [_VP, _VP, _VP, _VP, _I, _I, _I, _D, _VP, _VP]),
     "tor_bounds": (_I, [_VP, _VP, _VP, _VP, _I, _I, _D, _VP, _VP]),
@@ -385,6 +390,41 @@ def fixed_to_result(limbs, k: int, tier: str = "fp64") -> TorResult:
     out = TorResultC()
     _check(load_library().tor_fixed_to_result(arr, k, _PREC[tier], ctypes.byref(out)))
     return TorResult.from_c(out)
+
+
+def levels(O: torch.Tensor, prec: str = "fp64", level_prec=None, layout: str = "xxpp", stream=None) -> TorResult:
+    """tor_levels: Tor(O) by the paper's level-by-level schedule with a fresh elimination per
+    subset; level_prec: optional list of k + 1 tier names for the levels |Z| = 0..k."""
+    lib = load_library()
+    k, ld = _mat(O)
+    nbytes = ctypes.c_size_t()
+    rc = lib.tor_levels_workspace(k, O.device.index or 0, ctypes.byref(nbytes))
+    if rc:
+        raise TorError(rc, "tor_levels_workspace failed")
+    ws = torch.empty(max(nbytes.value, 1), dtype=torch.uint8, device=O.device)
+    out = torch.zeros(RESULT_BYTES, dtype=torch.uint8, device=O.device)
+    lp = None
+    if level_prec is not None:
+        if len(level_prec) != k + 1:
+            raise ValueError("level_prec needs k + 1 entries")
+        lp = (ctypes.c_int * (k + 1))(*[_PREC[p] for p in level_prec])
+    rc = lib.tor_levels(O.data_ptr(), k, ld, _LAYOUT[layout], _PREC[prec], lp, ws.data_ptr(), nbytes.value,
+                        _stream(stream), out.data_ptr())
+    if rc:
+        raise TorError(rc, lib.tor_levels_last_error().decode())
+    return TorResult.from_bytes(out.cpu().numpy().tobytes())
+
+
+def level_next_mask(mask: int) -> int:
+    """The next smaller mask with the same popcount (Algorithm 2); 0 when none is left."""
+    return int(load_library().tor_level_next_mask(mask & 0xFFFFFFFFFFFFFFFF))
+
+
+def level_kth_mask(k: int, m: int, r: int) -> int:
+    """The r-th mask of popcount m over k bits, in decreasing order (Algorithm 2)."""
+    out = ctypes.c_uint64()
+    _check(load_library().tor_level_kth_mask(k, m, r, ctypes.byref(out)))
+    return out.value
 
 
 def fx256_mul(a: torch.Tensor, b: torch.Tensor):
