@@ -362,6 +362,40 @@ def run_table(args):
     ctx.close()
 
 
+def run_levels(args):
+    """The prefix-tree walk against the paper's own schedule (a fresh elimination per subset,
+    level by level) on the same GPU, same tier, same instance."""
+    import torch
+    from paper_2009_01177_gb300 import gbs_inputs as gi
+    from paper_2009_01177_gb300 import tor
+    ctx = tor.Context(0)
+    st, pat, O32 = gi.workload_m100(32)
+    rows = {}
+    for k in (20, 24, 26):
+        Od = torch.from_numpy(gi.select(st.O, pat[:k])).cuda()
+        ctx.autotune(k, "fp64")
+        for name, fn in (("walk", lambda: ctx.single(Od, prec="fp64")),
+                         ("levels", lambda: tor.levels(Od, prec="fp64"))):
+            r = fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                r = fn()
+            torch.cuda.synchronize()
+            el = (time.perf_counter() - t0) / args.steps
+            rows.setdefault(f"k{k}", {})[name] = {"s": el, "subset_dets_per_s": 2.0 ** k / el, "tor": r.value,
+                                                  "err_est": r.err_est}
+        rows[f"k{k}"]["speedup_walk"] = rows[f"k{k}"]["levels"]["s"] / rows[f"k{k}"]["walk"]["s"]
+    line = {"metric": "prefix-tree walk vs the paper's level schedule (fresh elimination per subset)",
+            "value": rows["k26"]["speedup_walk"], "unit": "x", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic", "steps": args.steps,
+            "config": {"workload": "k = 20, 24, 26 patterns of the synthetic M=100 state (seed 2), FP64, "
+                                   "tor_single (autotuned) against tor_levels, wall time per call"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_batch(args):
     """Batched Tor/s for 4096 patterns (k in [8, 30]) against one launch per pattern."""
     import torch
@@ -639,7 +673,7 @@ def main():
     ap.add_argument("--k", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--mode", default="single", choices=["single", "batch", "mh", "adaptive", "table"])
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "mh", "adaptive", "table", "levels"])
     ap.add_argument("--table-m", type=int, default=26, help="table mode: modes M (2^M patterns)")
     ap.add_argument("--n", type=int, default=4096, help="patterns (batch) or chains (mh)")
     ap.add_argument("--chunk-bits", type=int, default=None,
@@ -663,6 +697,9 @@ def main():
         return
     if args.mode == "table":
         run_table(args)
+        return
+    if args.mode == "levels":
+        run_levels(args)
         return
 
     import torch
