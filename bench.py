@@ -99,6 +99,9 @@ def paper_flops(k):
     return float(sum(comb(k, i) * (32 * i ** 3 + 12 * i ** 2 - 8 * i) / 3 for i in range(1, k + 1)))
 
 
+DTYPE_OF = {"fp64": "f64", "dd": "f64x2 (double-double)", "fx128": "fixed128", "fx256": "fixed256"}
+
+
 def config(k, extra=None):
     c = {"workload": f"single Torontonian k={k} ({2 * k}x{2 * k} FP64 O_S) of a synthetic M=100 lossy "
                      f"GBS state (r~U[0.6,1.2], Haar U, eta=0.3, seed 2)",
@@ -675,6 +678,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--mode", default="single", choices=["single", "batch", "mh", "adaptive", "table", "levels"])
     ap.add_argument("--table-m", type=int, default=26, help="table mode: modes M (2^M patterns)")
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "dd", "fx128", "fx256"],
+                    help="single mode: the tier (the FP64 roofline applies to fp64 only)")
     ap.add_argument("--n", type=int, default=4096, help="patterns (batch) or chains (mh)")
     ap.add_argument("--chunk-bits", type=int, default=None,
                     help="single mode: chunk depth d instead of the autotuner's choice")
@@ -718,7 +723,7 @@ def main():
     peak_dfma, clk = ctx.fp64_peak()
     if args.chunk_bits is None:
         # the project's autotuner picks the chunk depth and blocks per SM for this k (about 20 s)
-        tuned_d, tuned_bps = ctx.autotune(k, "fp64")
+        tuned_d, tuned_bps = ctx.autotune(k, args.prec)
         launch_how = "autotuned"
     else:
         tuned_d, tuned_bps = args.chunk_bits, args.blocks_per_sm
@@ -730,7 +735,7 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     for _ in range(args.warmup):
-        ctx.single_async(Od, out, prec="fp64")
+        ctx.single_async(Od, out, prec=args.prec)
     torch.cuda.synchronize()
 
     def barrier():
@@ -747,7 +752,7 @@ def main():
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record()
-            ctx.single_async(Od, out, prec="fp64")
+            ctx.single_async(Od, out, prec=args.prec)
             ev[i][1].record()
             walk_ms.append(ctx.walk_time_ms())
         barrier()
@@ -763,7 +768,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         Od2.copy_(O_pin, non_blocking=True)
-        r_e2e = ctx.single(Od2, prec="fp64")
+        r_e2e = ctx.single(Od2, prec=args.prec)
     barrier()
     e2e_s = time.perf_counter() - t0
 
@@ -784,12 +789,12 @@ def main():
             cpu = {"value": n / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"{nch} random 256-subset chunks (masks [c 2^8, (c+1) 2^8)) of the same "
                              f"k={k} matrix, {el:.1f} s; 256-bit fixed point, OpenMP over masks"}
-        traffic = walk_traffic(k)
+        traffic = walk_traffic(k) if args.prec == "fp64" else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config(k, {"fp64_peak_frac": achieved / PEAK_TFLOPS, "chunk_bits": tuned_d,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_OF[args.prec], "data": "synthetic",
+            "config": config(k, {"tier": args.prec, "fp64_peak_frac": achieved / PEAK_TFLOPS, "chunk_bits": tuned_d,
                                  "blocks_per_sm": tuned_bps, "launch": launch_how}),
             "e2e": {"value": float(2 ** k) * args.steps * world / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(O.nbytes), "d2h_bytes_per_step": tor.RESULT_BYTES},
