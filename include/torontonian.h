@@ -100,7 +100,12 @@ typedef struct {
 
 /* ------------------------------------------------------------------ context */
 
-/* Create a context on CUDA device `device`.  Returns TOR_OK or an error. */
+/* Create a context on CUDA device `device`.  Returns TOR_OK or an error.
+ * A context owns its workspaces and is used by one host thread at a time
+ * (calls on it do not lock); separate contexts, on the same device or not,
+ * may be used concurrently.  tor_single_noalloc and tor_levels take no
+ * context: tor_levels uses only the caller's workspace, and concurrent
+ * tor_single_noalloc calls share one fixed array and serialise on it. */
 int tor_create(tor_ctx **ctx, int device);
 
 /* Release the context and its workspace (NULL is ignored). */
