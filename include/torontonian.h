@@ -104,8 +104,9 @@ typedef struct {
  * A context owns its workspaces and is used by one host thread at a time
  * (calls on it do not lock); separate contexts, on the same device or not,
  * may be used concurrently.  tor_single_noalloc and tor_levels take no
- * context: tor_levels uses only the caller's workspace, and concurrent
- * tor_single_noalloc calls share one fixed array and serialise on it. */
+ * context: tor_levels uses only the caller's workspace; tor_single_noalloc
+ * calls share one fixed array, so calls whose GPU work could overlap must be
+ * serialised by the caller. */
 int tor_create(tor_ctx **ctx, int device);
 
 /* Release the context and its workspace (NULL is ignored). */
