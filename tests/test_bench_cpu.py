@@ -1,0 +1,50 @@
+"""Host logic of bench.py (no GPU): the paper's FLOP model, the peak lookup, and the
+traffic figure that is reported only while the walk's sources are unchanged."""
+import json
+import os
+from math import comb
+
+import pytest
+
+import bench
+
+
+def test_paper_flop_model_counts_one_solve_per_subset():
+    # Sec. 7.1.2 (Eq. linflops): a complex HPD solve of size n = 2i costs 4/3 n^3 + n^2 - 4/3 n flops
+    for k in (1, 3, 10, 32):
+        direct = sum(comb(k, i) * (4 / 3 * (2 * i) ** 3 + (2 * i) ** 2 - 4 / 3 * (2 * i)) for i in range(1, k + 1))
+        assert bench.paper_flops(k) == pytest.approx(direct, rel=1e-12)
+    assert bench.paper_flops(1) == 12.0
+
+
+def test_hbm_peak_prefers_the_measured_file(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    v, src = bench.hbm_peak()
+    assert v == 6800.0 and "fallback" in src
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 7000.5}))
+    v, src = bench.hbm_peak()
+    assert v == 7000.5 and "measured" in src
+
+
+def test_walk_traffic_only_while_the_sources_match(tmp_path, monkeypatch):
+    # a copy of the walk's sources with a profile line keyed by their hash
+    src_dir = tmp_path / "paper_2009_01177_gb300" / "csrc"
+    src_dir.mkdir(parents=True)
+    for f in bench.WALK_SOURCES:
+        with open(os.path.join(bench.ROOT, f), "rb") as fh:
+            (tmp_path / f).write_bytes(fh.read())
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    sha = bench.walk_sources_sha256()
+    (tmp_path / "profiles" / "k_dfs_fp64_k32.md").write_text(
+        f"traffic_bytes_per_launch = 1.25e11 (walk sources sha256 {sha})\n")
+    assert bench.walk_traffic(32) == 1.25e11
+    assert bench.walk_traffic(30) is None                          # no summary for that size
+    with open(tmp_path / bench.WALK_SOURCES[0], "ab") as fh:       # any edit to the kernel's sources
+        fh.write(b"\n// changed\n")
+    assert bench.walk_traffic(32) is None
+
+
+def test_committed_summary_matches_the_committed_sources():
+    # the figure in the repository is for the sources in the repository
+    assert bench.walk_traffic(32) is not None
