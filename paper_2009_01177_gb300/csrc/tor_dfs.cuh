@@ -82,9 +82,9 @@ __device__ __forceinline__ void fx_add_signed(Fx256 &acc, double x, bool neg, in
 // ------------------------------------------------------- FP64 primitives
 // Tuning switches (compile time).  Defaults are the fastest measured on GB300
 // for the k = 32 workload: larger register subtrees, unrolled memory-tier
-// updates and the FP32-seeded reciprocal square root all shorten the FP64
-// instruction count but lengthen dependency chains or code, and the walk is
-// latency-bound rather than FP64-issue-bound.
+// updates and the FP32-seeded reciprocal square root each cut FP64 instructions
+// but lengthen dependency chains or code; with the FP64 pipe about 2/3 busy,
+// the added latency costs more than the saved issue slots.
 #ifndef TOR_F64_RREG
 #define TOR_F64_RREG 3
 #endif
