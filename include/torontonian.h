@@ -51,6 +51,7 @@ extern "C" {
 #endif
 
 #define TOR_MAX_K 64
+#define TOR_LEVELS_MAX_K 48   /* largest k tor_levels takes */
 
 enum {
     TOR_OK = 0,
@@ -232,7 +233,7 @@ int tor_all_patterns(tor_ctx *ctx, const double *O, int M, int ld, int prec, cud
  * exactly.  A second, independent GPU evaluation of Eq. 2 (another subset
  * order, another factorization of every term) for cross-checks beyond the CPU
  * oracle's reach; about k/3 times the work of tor_single's walk per subset.
- *   O, k, ld, layout   as for tor_single; k in [0, 48].
+ *   O, k, ld, layout   as for tor_single; k in [0, TOR_LEVELS_MAX_K].
  *   prec        TOR_PREC_FP64, TOR_PREC_DD or TOR_PREC_FX128 for every level,
  *   level_prec  host, k + 1 tiers for the levels m = 0..k (the paper's per-|Z|
  *               precision choice), or NULL to use prec throughout.

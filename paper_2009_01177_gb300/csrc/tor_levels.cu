@@ -23,8 +23,6 @@
 #include "tor_internal.h"
 #include "tor_walk.cuh"
 
-#define TOR_LEVELS_MAX_K 48
-
 namespace tor {
 namespace {
 
@@ -233,7 +231,7 @@ int tor_levels_workspace(int k, int device, size_t *bytes) {
 int tor_levels(const double *O, int k, int ld, int layout, int prec, const int *level_prec, void *workspace,
                size_t workspace_bytes, cudaStream_t s, tor_result *out_dev) {
   using namespace tor;
-  if (k < 0 || k > TOR_LEVELS_MAX_K) return lv_fail(TOR_EINVAL, "k outside [0, 48]");
+  if (k < 0 || k > TOR_LEVELS_MAX_K) return lv_fail(TOR_EINVAL, "k outside [0, TOR_LEVELS_MAX_K]");
   if ((k > 0 && !O) || !out_dev || !workspace) return lv_fail(TOR_EINVAL, "null pointer");
   if (k > 0 && ld < 2 * k) return lv_fail(TOR_EINVAL, "ld < 2k");
   if (layout != TOR_LAYOUT_XXPP && layout != TOR_LAYOUT_XPXP) return lv_fail(TOR_EINVAL, "bad layout");

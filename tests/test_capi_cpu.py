@@ -101,3 +101,69 @@ def test_shard_sums_of_384_bit_partials():
     assert tot.shape == (12,)
     lo, hi = shard.limbs_to_ints(tot)
     assert lo == (3 - (1 << 300)) % (1 << 384) and hi == (1 << 300) + 7
+
+
+def test_bad_arguments_are_refused_before_any_device_call(lib):
+    # every check below returns before the library touches CUDA, so it runs without a GPU
+    from paper_2009_01177_gb300 import tor
+    tor.load_library()
+    L = tor._lib
+    EINVAL = tor.TOR_EINVAL
+    O = np.eye(6)                                    # host memory: never dereferenced here
+    Op = O.ctypes.data_as(ctypes.c_void_p)
+    res = tor.TorResultC()
+    dummy = ctypes.c_void_p(O.ctypes.data)           # a non-null pointer for the output slots
+    XXPP, XPXP = 0, 1
+    hdr = open(HEADER).read()
+    MAX_K = int(re.search(r"#define TOR_MAX_K (\d+)", hdr).group(1))
+    LEVELS_MAX_K = int(re.search(r"#define TOR_LEVELS_MAX_K (\d+)", hdr).group(1))
+
+    # context calls with a null context
+    assert L.tor_single(None, Op, 3, 6, XXPP, tor.PREC_FP64, 0.0, None, ctypes.byref(res)) == EINVAL
+    assert "null context" in L.tor_last_error().decode()
+    assert L.tor_single_async(None, Op, 3, 6, XXPP, tor.PREC_FP64, None, dummy) == EINVAL
+    assert L.tor_chunks(None, Op, 3, 6, XXPP, tor.PREC_FP64, 1, 0, 2, None, dummy) == EINVAL
+    assert L.tor_all_patterns(None, Op, 3, 6, tor.PREC_FP64, None, dummy) == EINVAL
+    assert L.tor_batch_reserve(None, 16, 8) == EINVAL
+
+    # host-side conversion: null pointers and a tier that is not an explicit one
+    limbs = (ctypes.c_uint64 * 12)()
+    assert L.tor_fixed_to_result(None, 3, tor.PREC_FP64, ctypes.byref(res)) == EINVAL
+    assert L.tor_fixed_to_result(limbs, 3, tor.PREC_FP64, None) == EINVAL
+    assert L.tor_fixed_to_result(limbs, 3, tor.PREC_AUTO, ctypes.byref(res)) == EINVAL
+    assert L.tor_fixed_to_result(limbs, 3, tor.PREC_FX256 + 1, ctypes.byref(res)) == EINVAL
+
+    # the context-free single call
+    fp64 = tor.PREC_FP64
+    assert L.tor_single_noalloc(Op, MAX_K + 1, 2 * MAX_K + 2, XXPP, fp64, None, dummy) == EINVAL
+    assert L.tor_single_noalloc(None, 3, 6, XXPP, fp64, None, dummy) == EINVAL
+    assert L.tor_single_noalloc(Op, 3, 5, XXPP, fp64, None, dummy) == EINVAL
+    assert "ld = 5 < 2k = 6" in L.tor_last_error().decode()
+    assert L.tor_single_noalloc(Op, 3, 6, 7, fp64, None, dummy) == EINVAL
+    assert L.tor_single_noalloc(Op, 3, 6, XPXP, tor.PREC_FX128, None, dummy) == EINVAL
+    assert L.tor_single_noalloc(Op, 3, 6, XPXP, fp64, None, None) == EINVAL
+
+    # the level scheduler: sizes, pointers, layout and per-level tiers
+    ws = ctypes.c_void_p(O.ctypes.data)
+    nbytes = ctypes.c_size_t()
+    assert L.tor_levels_workspace(3, 0, None) == EINVAL
+    assert L.tor_levels_workspace(LEVELS_MAX_K + 1, 0, ctypes.byref(nbytes)) == EINVAL
+    assert L.tor_levels(Op, -1, 6, XXPP, fp64, None, ws, 1 << 20, None, dummy) == EINVAL
+    assert L.tor_levels(Op, LEVELS_MAX_K + 1, 200, XXPP, fp64, None, ws, 1 << 20, None, dummy) == EINVAL
+    assert L.tor_levels(None, 3, 6, XXPP, fp64, None, ws, 1 << 20, None, dummy) == EINVAL
+    assert L.tor_levels(Op, 3, 6, XXPP, fp64, None, None, 1 << 20, None, dummy) == EINVAL
+    assert L.tor_levels(Op, 3, 6, XXPP, fp64, None, ws, 1 << 20, None, None) == EINVAL
+    assert L.tor_levels(Op, 3, 5, XXPP, fp64, None, ws, 1 << 20, None, dummy) == EINVAL
+    assert L.tor_levels(Op, 3, 6, 2, fp64, None, ws, 1 << 20, None, dummy) == EINVAL
+    for bad in (tor.PREC_AUTO, tor.PREC_FX256):
+        tiers = (ctypes.c_int * 4)(fp64, fp64, bad, fp64)
+        assert L.tor_levels(Op, 3, 6, XXPP, fp64, tiers, ws, 1 << 20, None, dummy) == EINVAL
+        assert "level tiers" in L.tor_levels_last_error().decode()
+    mask = ctypes.c_uint64()
+    assert L.tor_level_kth_mask(3, 4, 0, ctypes.byref(mask)) == EINVAL
+    assert L.tor_level_kth_mask(3, 1, 0, None) == EINVAL
+    assert L.tor_level_kth_mask(3, 1, 3, ctypes.byref(mask)) == EINVAL   # C(3, 1) = 3 ranks
+
+    # the 256-bit product helper
+    assert L.tor_fx256_mul(None, None, -1, None, None, None) == EINVAL
+    assert L.tor_fx256_mul(None, dummy, 1, dummy, dummy, None) == EINVAL
