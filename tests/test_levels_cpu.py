@@ -1,4 +1,5 @@
 """Algorithm 2's mask functions (host code of the library; no GPU)."""
+import os
 from itertools import combinations
 from math import comb
 
@@ -12,9 +13,21 @@ def lib():
     tor.load_library()
 
 
+def golden_next_masks():
+    path = os.path.join(os.path.dirname(__file__), "golden", "alg2_next_mask.txt")
+    rows = [line.split() for line in open(path) if line.strip() and not line.startswith("#")]
+    return [(int(n), int(a, 2), int(b, 2)) for n, a, b in rows]
+
+
 def test_paper_worked_example():
-    # Sec. 4.1: the mask after 010011 is 001110
-    assert tor.level_next_mask(0b010011) == 0b001110
+    cases = golden_next_masks()
+    assert cases
+    for n, mask, nxt in cases:
+        assert tor.level_next_mask(mask) == nxt
+        # the same two masks are consecutive ranks of their level
+        m = bin(mask).count("1")
+        r = next(r for r in range(comb(n, m)) if tor.level_kth_mask(n, m, r) == mask)
+        assert tor.level_kth_mask(n, m, r + 1) == nxt
 
 
 @pytest.mark.parametrize("k", [1, 5, 8, 10])
