@@ -91,6 +91,16 @@ def hbm_peak():
         return 6800.0, "of fallback (6.8 TB/s)"
 
 
+def dram_rate(traffic, kernel_ms):
+    """The kernel's measured DRAM traffic over its live-timed duration, against the HBM copy peak
+    (the walk is not memory-bound; this shows by how far), or None without a traffic figure."""
+    if traffic is None or not kernel_ms:
+        return None
+    peak, src = hbm_peak()
+    gbs = traffic / (kernel_ms * 1e-3) / 1e9
+    return {"gbs": gbs, "frac_of_hbm": gbs / peak, "hbm_peak_gbs": peak, "peak_source": src}
+
+
 def paper_flops(k):
     """The paper's operation count for one Torontonian of k modes (Sec. 7.1.2, Eq. tflops): a
     Hermitian positive definite complex solve of size n = 2i, 4/3 n^3 + n^2 - 4/3 n flops
@@ -804,7 +814,7 @@ def main():
                          "kernel": "k_dfs<TierF64>", "kernel_ms": walk_avg,
                          "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2 flops",
                          "measured_dfma_tflops": 2 * peak_dfma / 1e12,
-                         "flops_per_subset": FLOPS_PER_SUBSET},
+                         "flops_per_subset": FLOPS_PER_SUBSET, "dram": dram_rate(traffic, walk_avg)},
             "paper_equivalent": {"tflops": paper_flops(k) / (walk_avg * 1e-3) / 1e12,
                                  "flops_per_launch": paper_flops(k),
                                  "note": "the paper's FLOP count of Eq. tflops (a fresh complex solve per "

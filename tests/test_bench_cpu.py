@@ -48,3 +48,11 @@ def test_walk_traffic_only_while_the_sources_match(tmp_path, monkeypatch):
 def test_committed_summary_matches_the_committed_sources():
     # the figure in the repository is for the sources in the repository
     assert bench.walk_traffic(32) is not None
+
+
+def test_dram_rate_of_the_walk(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.dram_rate(None, 291.7) is None
+    d = bench.dram_rate(1.1757e11, 291.7)                 # 117.6 GB in 291.7 ms
+    assert d["gbs"] == pytest.approx(403.05, rel=1e-3)
+    assert d["frac_of_hbm"] == pytest.approx(403.05 / 6800.0, rel=1e-3) and "fallback" in d["peak_source"]
