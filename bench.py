@@ -45,6 +45,18 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def max_over_ranks(values, world, device):
+    """Each value's maximum over the ranks of the default process group (the slowest rank's
+    time sets a weak-scaling step); the values unchanged at world size 1."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 def workload(k, rank):
     from paper_2009_01177_gb300 import gbs_inputs as gi
     st, pat, O = gi.workload_m100(k, seed=2, pattern_seed=None if rank == 0 else 2000 + rank)
@@ -782,11 +794,7 @@ def main():
     barrier()
     e2e_s = time.perf_counter() - t0
 
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_s, e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s, e2e_s = float(t[0]), float(t[1])
+    total_s, e2e_s = max_over_ranks([total_s, e2e_s], world, dev)
 
     if rank == 0:
         units = float(2 ** k) * args.steps * world

@@ -56,3 +56,28 @@ def test_dram_rate_of_the_walk(tmp_path, monkeypatch):
     d = bench.dram_rate(1.1757e11, 291.7)                 # 117.6 GB in 291.7 ms
     assert d["gbs"] == pytest.approx(403.05, rel=1e-3)
     assert d["frac_of_hbm"] == pytest.approx(403.05 / 6800.0, rel=1e-3) and "fallback" in d["peak_source"]
+
+
+def _max_rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    out[rank] = bench.max_over_ranks([1.0 + rank, 5.0 - rank], world, "cpu")
+    dist.destroy_process_group()
+
+
+def test_step_time_is_the_max_over_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    assert bench.max_over_ranks([2.5, 3], 1, "cpu") == [2.5, 3.0]
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        port = 29700 + os.getpid() % 1000
+        procs = [ctx.Process(target=_max_rank_main, args=(r, 2, port, out)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(120)
+        assert all(p.exitcode == 0 for p in procs)
+        assert out[0] == out[1] == [2.0, 5.0]
