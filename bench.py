@@ -3,16 +3,21 @@
 
 Workload: the Torontonian of a k = 32 click pattern (64 x 64 FP64 matrix,
 2^32 subsets) of a synthetic M = 100 mode lossy GBS state (r ~ U[0.6, 1.2],
-Haar U, eta = 0.3, seed 2), FP64 tier.  One step = one full Torontonian:
-prep (I - O, basis) + chunk roots + depth-first walk + exact reduction.
+Haar U, eta = 0.3, seed 2).  One step = one full Torontonian through the
+library's AUTO path with tol = 1e-10: the FP32 bound pass routes the instance
+to the tier that resolves it (the 256-bit-class fixed point at this kappa,
+about 1e28), then prep (I - O, basis) + chunk roots + depth-first walk + exact
+reduction, and the result's a-posteriori bound is checked against tol (the
+run exits non-zero when it is missed).  The FP64 walk on the same instance is
+reported beside it as a kernel-quality figure only: it does not resolve Tor.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
   python bench.py --mode batch   # 4096 click patterns, one scheduled batch vs one launch each
   python bench.py --mode mh      # MH sampling, learned vs plain proposal (M = 60; TV at M = 20)
 
-Prints one JSON line on rank 0.  Under torchrun (N > 1) each rank evaluates
-the Torontonian of its own click pattern of the same state (independent
-problems, no data-path collective: weak scaling).
+Prints one JSON line on rank 0.  Under torchrun (N > 1) the ranks split the
+chunks of the one Torontonian (Algorithm 1's rank partition) and add their
+exact partial sums with one all-gather (strong scaling).
 
 --impl reference times the CPU oracle (256-bit fixed-point direct subset
 sum, test infrastructure) on a bounded sample of the same workload.
@@ -63,33 +68,78 @@ def workload(k, rank):
     return st, pat, O
 
 
-# sources that define the single-instance FP64 walk kernel: a recorded DRAM
+# sources whose compiled kernel a recorded ncu figure belongs to: a DRAM
 # traffic figure is reported only while they are unchanged
-WALK_SOURCES = ["paper_2009_01177_gb300/csrc/" + f for f in
-                ("tor_dfs.cuh", "tor_walk.cuh", "tor_kernels.cu", "fx128.cuh", "tor_internal.h", "capi.cu")]
+_CSRC = "paper_2009_01177_gb300/csrc/"
+KERNEL_SOURCES = {
+    "k_dfs_fx9": [_CSRC + f for f in ("fx9.cuh", "tor_fx9.cuh", "fixacc.cuh", "tor_dfs.cuh", "tor_walk.cuh",
+                                      "tor_kernels.cu", "tor_internal.h", "capi.cu")],
+    "k_dfs_fp64": [_CSRC + f for f in ("tor_dfs.cuh", "tor_walk.cuh", "fixacc.cuh", "dd.cuh", "fx128.cuh",
+                                       "tor_kernels.cu", "tor_internal.h", "capi.cu")],
+}
 
 
-def walk_sources_sha256():
+def sources_sha256(kernel):
     import hashlib
     h = hashlib.sha256()
-    for f in WALK_SOURCES:
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def walk_traffic(k):
-    """DRAM bytes per k_dfs launch from the committed ncu summary, if taken on these sources."""
+def recorded_traffic(kernel, k):
+    """DRAM bytes per launch of `kernel` at k from the committed ncu summary
+    profiles/<kernel>_k<k>.md, if it was taken on the current sources."""
     import re
-    path = os.path.join(ROOT, "profiles", f"k_dfs_fp64_k{k}.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_k{k}.md")
     try:
         text = open(path).read()
     except OSError:
         return None
-    m = re.search(r"traffic_bytes_per_launch = ([0-9.eE+]+) \(walk sources sha256 ([0-9a-f]{64})\)", text)
-    if not m or m.group(2) != walk_sources_sha256():
+    m = re.search(r"traffic_bytes_per_launch = ([0-9.eE+]+) \(sources sha256 ([0-9a-f]{64})\)", text)
+    if not m or m.group(2) != sources_sha256(kernel):
         return None
     return float(m.group(1))
+
+
+TIER_NAME = {1: "fp64", 2: "dd", 3: "fx128", 4: "fx256"}
+# the 256-bit-class tier's limb products: a product of two nine-limb values
+# forms the limb pairs i + j >= 6, 60 signed 32 x 32 -> 64-bit multiply-adds
+MAC_PER_PRODUCT = 60
+
+
+def walk_ops(r):
+    """Operations of the depth-first walk over the 2^r subsets of r modes (the prefix tree of
+    Eq. 2's subsets, each child's Schur complement from its parent's): (pivot steps, pivot
+    coefficient sets, pivot rows, Schur entries updated, subsets)."""
+    import functools
+
+    @functools.lru_cache(None)
+    def node(m):
+        p = c = rows = e = n = 0
+        for cur in range(m):
+            p += 1
+            n += 1
+            if cur > 0:
+                c += 1
+                rows += 2 * cur
+                e += cur * (2 * cur + 1)
+                a = node(cur)
+                p, c, rows, e, n = p + a[0], c + a[1], rows + a[2], e + a[3], n + a[4]
+        return p, c, rows, e, n
+
+    p, c, rows, e, n = node(r)
+    return p, c, rows, e, n + 1
+
+
+def fx256_macs_per_subset(k):
+    """Algorithmic limb multiply-adds per subset of the 256-bit-class walk: per subset its
+    pivot (2x2 determinant: 2 products, two Newton steps of the reciprocal square root: 6,
+    the term t y: 1), per non-leaf pivot the coefficients D^-1 (4), per pivot row the
+    vector D^-1 u (4), per Schur entry the rank-2 update (2); each product 60 MACs."""
+    p, c, rows, e, n = walk_ops(k)
+    return MAC_PER_PRODUCT * (9 * p + 4 * c + 4 * rows + 2 * e) / n
 
 
 def hbm_peak():
@@ -121,13 +171,14 @@ def paper_flops(k):
     return float(sum(comb(k, i) * (32 * i ** 3 + 12 * i ** 2 - 8 * i) / 3 for i in range(1, k + 1)))
 
 
-DTYPE_OF = {"fp64": "f64", "dd": "f64x2 (double-double)", "fx128": "fixed128", "fx256": "fixed256"}
+DTYPE_OF = {"fp64": "f64", "dd": "f64x2 (double-double)", "fx128": "fixed128",
+            "fx256": "fixed256 (nine 29-bit i32 limbs, 203 fraction bits)"}
 
 
 def config(k, extra=None):
     c = {"workload": f"single Torontonian k={k} ({2 * k}x{2 * k} FP64 O_S) of a synthetic M=100 lossy "
                      f"GBS state (r~U[0.6,1.2], Haar U, eta=0.3, seed 2)",
-         "k": k, "subsets_per_step": 2 ** k, "tier": "fp64",
+         "k": k, "subsets_per_step": 2 ** k,
          "l2": "flushed between timed steps (256 MiB device write)"}
     if extra:
         c.update(extra)
@@ -689,6 +740,215 @@ def run_mh(args):
     ctx.close()
 
 
+def _timed_walks(ctx, Od, prec, reps):
+    """Walk-kernel milliseconds of `reps` single_async calls at an explicit tier, and the last result."""
+    import torch
+    from paper_2009_01177_gb300 import tor
+    out = torch.empty(tor.RESULT_BYTES, dtype=torch.uint8, device=Od.device)
+    ctx.single_async(Od, out, prec=prec)
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    ms = []
+    for _ in range(reps):
+        ctx.single_async(Od, out, prec=prec)
+        ms.append(ctx.walk_time_ms())
+    ctx.set_timing(False)
+    return ms, tor.TorResult.from_bytes(out.cpu().numpy().tobytes())
+
+
+def run_single(args):
+    """One Torontonian per step, routed by the bound pass to the tier that resolves it and
+    checked against tol; on N > 1 ranks the chunks of that one Torontonian are split."""
+    import math
+    import torch
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2009_01177_gb300 import tor
+    k, tol = args.k, args.tol
+    st, pat, O = workload(k, 0)
+    ctx = tor.Context(local)
+    Od = torch.from_numpy(O).to(dev)
+    bd = ctx.bounds([Od], tol=tol)[0]
+    routed = TIER_NAME[int(bd["tier"])]
+    tier = routed if args.prec == "auto" else args.prec
+    route = {"tol": tol, "requested": args.prec, "routed_tier": routed,
+             "bits_needed": float(bd["bits_needed"]), "log2_tmax": float(bd["log_tmax"]) / math.log(2),
+             "log2_kappa_est": float(bd["log_kappa_est"]) / math.log(2)}
+    if args.chunk_bits is None:
+        # the project's autotuner picks the chunk depth and blocks per SM for this k and tier
+        tuned_d, tuned_bps = ctx.autotune(k, tier)
+        launch_how = "autotuned"
+    else:
+        tuned_d, tuned_bps = args.chunk_bits, args.blocks_per_sm
+        ctx.set_chunk_bits(tuned_d)
+        ctx.set_launch(128, tuned_bps)
+        launch_how = "given"
+    if world > 1:
+        return run_sharded(args, ctx, Od, k, tier, tuned_d, route, rank, world, dev)
+
+    peak_dfma, clk = ctx.fp64_peak()
+    peak_mad = ctx.int_peak()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        ctx.single(Od, prec=args.prec, tol=tol)
+    torch.cuda.synchronize()
+
+    ctx.set_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    walk_ms, results = [], []
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record()
+            results.append(ctx.single(Od, prec=args.prec, tol=tol))   # bound pass, walk, result to host
+            ev[i][1].record()
+            walk_ms.append(ctx.walk_time_ms())
+        torch.cuda.synchronize()
+    ctx.set_timing(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    res = results[-1]
+
+    # end to end: pinned host input -> device, the same call, the result on the host; wall clock
+    O_pin = torch.from_numpy(O).pin_memory()
+    Od2 = torch.empty_like(Od)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Od2.copy_(O_pin, non_blocking=True)
+        r_e2e = ctx.single(Od2, prec=args.prec, tol=tol)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+
+    # the FP64 walk on the same instance: kernel quality only, it does not resolve this kappa
+    fp64 = None
+    if not args.no_fp64 and tier != "fp64":
+        if args.chunk_bits is None:
+            ctx.autotune(k, "fp64")
+        ms64, r64 = _timed_walks(ctx, Od, "fp64", 3)
+        w64 = float(np.mean(ms64))
+        t64 = FLOPS_PER_SUBSET * 2 ** k / (w64 * 1e-3) / 1e12
+        fp64 = {"kernel": "k_dfs<TierF64>", "subset_dets_per_s": 2 ** k / (w64 * 1e-3), "kernel_ms": w64,
+                "tflops": t64, "frac_of_fp64_peak": t64 / PEAK_TFLOPS,
+                "measured_dfma_tflops": 2 * peak_dfma / 1e12, "flops_per_subset": FLOPS_PER_SUBSET,
+                "err_est_over_tor": r64.err_est / abs(r64.value) if r64.value else None,
+                "resolved": bool(r64.err_est <= tol * abs(r64.value)),
+                "traffic": recorded_traffic("k_dfs_fp64", k),
+                "note": "FP64 tier timed on the same instance; its error bound exceeds |Tor| at this "
+                        "kappa, so it is a kernel-quality figure, not a Torontonian"}
+
+    units = float(2 ** k) * args.steps
+    value = units / total_s
+    walk_avg = float(np.mean(walk_ms))
+    resolved = bool(res.status == 0 and res.err_est <= tol * abs(res.value))
+    kernel = "k_dfs_fx9" if res.tier == 4 else "k_dfs<%s>" % TIER_NAME[res.tier]
+    if res.tier == 4:
+        macs = fx256_macs_per_subset(k)
+        achieved = macs * 2 ** k / (walk_avg * 1e-3) / 1e12
+        traffic = recorded_traffic("k_dfs_fx9", k)
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak_mad / 1e12, "unit": "T int32-MAC/s",
+                    "frac": achieved / (peak_mad / 1e12), "traffic": traffic, "kernel": kernel,
+                    "kernel_ms": walk_avg,
+                    "peak_source": "measured: independent mad.wide.s32 chains on all SMs (tor_int_peak), "
+                                   "the limb product of the 256-bit-class arithmetic",
+                    "macs_per_subset": macs,
+                    "derivation": "per subset: 2x2 det 2 + two Newton steps 6 + term 1 products, 0.5 "
+                                  "coefficient sets x 4, 2 pivot rows x 4, 7 Schur entries x 2 = 33 "
+                                  "products of 60 limb MACs (walk over all 2^k subsets)",
+                    "dram": dram_rate(traffic, walk_avg)}
+    else:
+        achieved = FLOPS_PER_SUBSET * 2 ** k / (walk_avg * 1e-3) / 1e12
+        traffic = recorded_traffic("k_dfs_fp64", k) if res.tier == 1 else None
+        roofline = {"bound": "alu", "achieved": achieved, "peak": PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / PEAK_TFLOPS, "traffic": traffic, "kernel": kernel,
+                    "kernel_ms": walk_avg, "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2",
+                    "flops_per_subset": FLOPS_PER_SUBSET}
+    cpu = None
+    if not args.no_cpu_baseline:
+        n, el, nch = cpu_oracle_sample(O, k, budget_s=args.cpu_budget)
+        cpu = {"value": n / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{nch} random 256-subset chunks (masks [c 2^8, (c+1) 2^8)) of the same "
+                         f"k={k} matrix, {el:.1f} s; 256-bit fixed point, OpenMP over masks"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_OF[TIER_NAME[res.tier]], "data": "synthetic",
+        "config": config(k, {"tier": TIER_NAME[res.tier], "route": route, "chunk_bits": tuned_d,
+                             "blocks_per_sm": tuned_bps, "launch": launch_how}),
+        "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(O.nbytes),
+                "d2h_bytes_per_step": tor.RESULT_BYTES},
+        "gpu_launches": 4 * args.steps,
+        "roofline": roofline,
+        "fp64_walk": fp64,
+        "paper_equivalent": {"tflops": paper_flops(k) / (walk_avg * 1e-3) / 1e12, "flops_per_launch": paper_flops(k),
+                             "note": "the paper's FLOP count of Eq. tflops (a fresh complex solve per "
+                                     "subset) over the walk time"},
+        "cpu_baseline": cpu,
+        "clocks": clocks.summary(),
+        "result": {"tor": res.value, "hi": res.hi, "lo": res.lo, "sum_abs": res.sum_abs,
+                   "err_est": res.err_est, "err_est_over_tor": res.err_est / abs(res.value) if res.value else None,
+                   "kappa": res.kappa, "tier": TIER_NAME[res.tier], "resolved": resolved,
+                   "steps_identical": len({(r.hi, r.lo) for r in results}) == 1,
+                   "e2e_equal": (r_e2e.hi, r_e2e.lo) == (res.hi, res.lo)},
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if not resolved:
+        sys.stderr.write(f"error bound {res.err_est:.3e} exceeds tol * |Tor| = {tol * abs(res.value):.3e}\n")
+        sys.exit(3)
+
+
+def run_sharded(args, ctx, Od, k, tier, d, route, rank, world, dev):
+    """N > 1: the 2^d chunks of the one Torontonian split over the ranks (Algorithm 1's rank
+    partition), each rank's exact partial sum all-gathered and added (the only exchange)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2009_01177_gb300 import shard, tor
+
+    def step():
+        r, _ = shard.tor_sharded(ctx, Od, d, tier)
+        return r
+
+    for _ in range(args.warmup):
+        step()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clocks:
+        dist.barrier()
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            ev[i][0].record()
+            res = step()
+            ev[i][1].record()
+        dist.barrier()
+        torch.cuda.synchronize()
+    total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    total_s, = max_over_ranks([total_s], world, dev)
+    resolved = bool(res.status == 0 and res.err_est <= args.tol * abs(res.value))
+    if rank == 0:
+        units = float(2 ** k) * args.steps
+        line = {"metric": METRIC, "value": units / total_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": DTYPE_OF[tier], "data": "synthetic",
+                "config": config(k, {"tier": tier, "route": route, "chunk_bits": d,
+                                     "parallelism": f"chunk ranges over {world} ranks, exact all-gather",
+                                     "l2": "not flushed (the sharded step's inputs are one 2k x 2k matrix)"}),
+                "gpu_launches": 3 * args.steps,
+                "clocks": clocks.summary(),
+                "result": {"tor": res.value, "err_est": res.err_est, "tier": tier, "resolved": resolved}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    dist.destroy_process_group()
+    if not resolved:
+        sys.exit(3)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -700,8 +960,11 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--mode", default="single", choices=["single", "batch", "mh", "adaptive", "table", "levels"])
     ap.add_argument("--table-m", type=int, default=26, help="table mode: modes M (2^M patterns)")
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "dd", "fx128", "fx256"],
-                    help="single mode: the tier (the FP64 roofline applies to fp64 only)")
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "dd", "fx128", "fx256"],
+                    help="single mode: AUTO (the bound pass routes to the tier that meets --tol, escalating "
+                         "on the a-posteriori bound) or an explicit tier")
+    ap.add_argument("--tol", type=float, default=1e-10, help="relative tolerance every result must meet")
+    ap.add_argument("--no-fp64", action="store_true", help="single mode: skip the secondary FP64 walk timing")
     ap.add_argument("--n", type=int, default=4096, help="patterns (batch) or chains (mh)")
     ap.add_argument("--chunk-bits", type=int, default=None,
                     help="single mode: chunk depth d instead of the autotuner's choice")
@@ -729,114 +992,7 @@ def main():
         run_levels(args)
         return
 
-    import torch
-    rank, world, local = env_rank()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-
-    from paper_2009_01177_gb300 import tor
-    k = args.k
-    st, pat, O = workload(k, rank)
-    ctx = tor.Context(local)
-    peak_dfma, clk = ctx.fp64_peak()
-    if args.chunk_bits is None:
-        # the project's autotuner picks the chunk depth and blocks per SM for this k (about 20 s)
-        tuned_d, tuned_bps = ctx.autotune(k, args.prec)
-        launch_how = "autotuned"
-    else:
-        tuned_d, tuned_bps = args.chunk_bits, args.blocks_per_sm
-        ctx.set_chunk_bits(tuned_d)
-        ctx.set_launch(128, tuned_bps)
-        launch_how = "given"
-    Od = torch.from_numpy(O).to(dev)
-    out = torch.empty(tor.RESULT_BYTES, dtype=torch.uint8, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-
-    for _ in range(args.warmup):
-        ctx.single_async(Od, out, prec=args.prec)
-    torch.cuda.synchronize()
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-
-    ctx.set_timing(True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    walk_ms = []
-    with ClockSampler(local) as clocks:
-        barrier()
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record()
-            ctx.single_async(Od, out, prec=args.prec)
-            ev[i][1].record()
-            walk_ms.append(ctx.walk_time_ms())
-        barrier()
-    ctx.set_timing(False)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1e3
-    res = tor.TorResult.from_bytes(out.cpu().numpy().tobytes())
-
-    # end to end: pinned host input -> device, call, host result; wall clock
-    O_pin = torch.from_numpy(O).pin_memory()
-    Od2 = torch.empty_like(Od)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        Od2.copy_(O_pin, non_blocking=True)
-        r_e2e = ctx.single(Od2, prec=args.prec)
-    barrier()
-    e2e_s = time.perf_counter() - t0
-
-    total_s, e2e_s = max_over_ranks([total_s, e2e_s], world, dev)
-
-    if rank == 0:
-        units = float(2 ** k) * args.steps * world
-        value = units / total_s
-        walk_avg = sum(walk_ms) / len(walk_ms)
-        achieved = FLOPS_PER_SUBSET * 2 ** k / (walk_avg * 1e-3) / 1e12
-        cpu = None
-        if world == 1 and not args.no_cpu_baseline:
-            n, el, nch = cpu_oracle_sample(O, k, budget_s=args.cpu_budget)
-            cpu = {"value": n / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                   "sample": f"{nch} random 256-subset chunks (masks [c 2^8, (c+1) 2^8)) of the same "
-                             f"k={k} matrix, {el:.1f} s; 256-bit fixed point, OpenMP over masks"}
-        traffic = walk_traffic(k) if args.prec == "fp64" else None
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_OF[args.prec], "data": "synthetic",
-            "config": config(k, {"tier": args.prec, "fp64_peak_frac": achieved / PEAK_TFLOPS, "chunk_bits": tuned_d,
-                                 "blocks_per_sm": tuned_bps, "launch": launch_how}),
-            "e2e": {"value": float(2 ** k) * args.steps * world / e2e_s, "unit": UNIT,
-                    "h2d_bytes_per_step": int(O.nbytes), "d2h_bytes_per_step": tor.RESULT_BYTES},
-            "gpu_launches": 3 * args.steps,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / PEAK_TFLOPS, "traffic": traffic,
-                         "kernel": "k_dfs<TierF64>", "kernel_ms": walk_avg,
-                         "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2 flops",
-                         "measured_dfma_tflops": 2 * peak_dfma / 1e12,
-                         "flops_per_subset": FLOPS_PER_SUBSET, "dram": dram_rate(traffic, walk_avg)},
-            "paper_equivalent": {"tflops": paper_flops(k) / (walk_avg * 1e-3) / 1e12,
-                                 "flops_per_launch": paper_flops(k),
-                                 "note": "the paper's FLOP count of Eq. tflops (a fresh complex solve per "
-                                         "subset) over the walk time; the incremental walk executes "
-                                         "about 55 flops per subset instead"},
-            "cpu_baseline": cpu,
-            "clocks": clocks.summary(),
-            "result": {"tor": res.value, "sum_abs": res.sum_abs, "err_est": res.err_est,
-                       "kappa": res.kappa, "e2e_equal": (r_e2e.hi, r_e2e.lo) == (res.hi, res.lo)},
-        }
-        print(json.dumps(line), flush=True)
-    ctx.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    run_single(args)
 
 
 if __name__ == "__main__":

@@ -72,11 +72,13 @@ enum { TOR_PREC_AUTO = 0, TOR_PREC_FP64 = 1, TOR_PREC_DD = 2, TOR_PREC_FX128 = 3
  * that still leaves the range sets the result's status to TOR_EINVAL.
  * Available in tor_single, tor_single_async, tor_chunks and tor_batch (the
  * asynchronous single and chunk calls do not run the range check).
- * TOR_PREC_FX256: the paper's 256-bit mode, 192 fraction bits; intermediates
- * below 2^63, so t_max <= 2^30 is required.  Its terms carry 192 fraction
- * bits, so its exact partial sums are 384-bit: tor_chunks writes 12 limbs per
- * chunk for it (two 6-limb values with 192 fraction bits) instead of 8.
- * Available in tor_single, tor_single_async and tor_chunks; batches refuse it. */
+ * TOR_PREC_FX256: the paper's 256-bit mode (Sec. 5.1-5.2) in nine 29-bit
+ * signed limbs: 203 fraction bits, magnitudes below 2^57, so t_max <= 2^26 is
+ * required (the pivot inverses reach t_max^2, the Schur coefficients a few
+ * times that).  Its exact partial sums are 512-bit with 256 fraction bits:
+ * tor_chunks writes 16 limbs per chunk for it (two 8-limb values) instead of
+ * 8, and a chunk walks at most 2^34 subsets (k - chunk_bits <= 34).
+ * Available in tor_single, tor_single_async, tor_chunks and tor_batch. */
 enum { TOR_LAYOUT_XXPP = 0, TOR_LAYOUT_XPXP = 1 };
 
 typedef struct tor_ctx tor_ctx;
@@ -135,7 +137,7 @@ int tor_set_chunk_bits(tor_ctx *ctx, int chunk_bits);
  *         tier for relative tolerance `tol`; while the result's a-posteriori
  *         bound err_est exceeds tol * |Tor| it is recomputed in the next tier
  *         with more precision that fits the instance's range (FP64 -> FX128
- *         when t_max <= 2^11, else FX256 when t_max <= 2^30, else
+ *         when t_max <= 2^11, else FX256 when t_max <= 2^26, else
  *         double-double; FX128 -> FX256 or double-double; double-double ->
  *         FX256), and when none is left the call returns TOR_EPREC with the
  *         result filled in.  `tol` is ignored for the explicit tiers; the
@@ -174,8 +176,9 @@ int tor_single_async(tor_ctx *ctx, const double *O, int k, int ld, int layout, i
  *               (-1)^(k-|Z|) t_Z and of t_Z, each a 256-bit two's-complement
  *               fixed-point number with 128 fractional bits, little-endian
  *               64-bit limbs (limbs 0..3 = signed sum, 4..7 = sum_abs).  For
- *               TOR_PREC_FX256: x 12 uint64, two 384-bit values with 192
- *               fractional bits (limbs 0..5 and 6..11).
+ *               TOR_PREC_FX256: x 16 uint64, two 512-bit values with 256
+ *               fractional bits (limbs 0..7 and 8..15); its chunks walk at
+ *               most 2^34 subsets (k - chunk_bits <= 34, else TOR_EINVAL).
  *   Partials of disjoint ranges add exactly (integer addition), so any split
  *   gives the same total bit for bit.
  */
@@ -255,17 +258,17 @@ const char *tor_levels_last_error(void);
 uint64_t tor_level_next_mask(uint64_t mask);
 int tor_level_kth_mask(int k, int m, uint64_t r, uint64_t *mask);
 
-/* tor_fx256_mul: n elementwise products of 256-bit fixed-point numbers exactly
- * as the TOR_PREC_FX256 tier forms them (Sec. 5.1-5.3: magnitudes multiplied,
- * truncated to 192 fraction bits, sign restored), so that the arithmetic can
- * be checked against an independent big-integer evaluation.
- *   a_dev, b_dev  dev, n x 4 uint64: two's-complement values / 2^192,
- *                 little-endian limbs.
- *   out_dev       dev, n x 4 uint64 products.   ovf_dev  dev, n ints: 1 where
- *                 the product's magnitude does not fit in 255 bits.
- * Asynchronous on `stream`.  TOR_EINVAL for n < 0 or null pointers. */
-int tor_fx256_mul(const uint64_t *a_dev, const uint64_t *b_dev, int n, uint64_t *out_dev, int *ovf_dev,
-                  cudaStream_t stream);
+/* tor_fx256_fma2: n elementwise s + a1 b1 + a2 b2 exactly as the
+ * TOR_PREC_FX256 walk forms its Schur updates (Sec. 4.2 elimination in the
+ * fixed point of Sec. 5.1-5.2), exposed so tests can check the arithmetic bit
+ * for bit.  Each operand is n x 9 int32 limbs on the device, value
+ * sum_i l_i 2^(29 i - 203) (any limbs below 2^29 in magnitude); the result
+ * is n x 9 limbs in [-2^28, 2^28): the exact sum of the product columns
+ * c >= 6 (limb pairs i + j >= 6) and of s, rounded to nearest at 2^-203
+ * (ties up); ovf_dev[i] = 1 when its magnitude reaches 2^57.  Asynchronous on
+ * `stream`; TOR_EINVAL for n < 0 or null pointers. */
+int tor_fx256_fma2(const int32_t *s_dev, const int32_t *a1_dev, const int32_t *b1_dev, const int32_t *a2_dev,
+                   const int32_t *b2_dev, int n, int32_t *out_dev, int *ovf_dev, cudaStream_t stream);
 
 /* Convert one fixed-point pair as written by tor_chunks (8 limbs, or 12 for
  * TOR_PREC_FX256), possibly summed over shards, to a tor_result (host, no
@@ -330,8 +333,7 @@ int tor_batch_reserve(tor_ctx *ctx, int n_max, int k_max);
  * a-posteriori bound and escalate), else TOR_PREC_FX128 if t_max <= 2^11 and
  * bits_needed <= 120 (the fixed-point unit's 100 bits plus the same slack),
  * else TOR_PREC_DD if bits_needed <= 124, else TOR_PREC_FX256 if
- * t_max <= 2^30, else TOR_PREC_DD (batches, which have no 256-bit tier, run
- * TOR_PREC_FX256 routes in double-double).  B not positive definite in FP32
+ * t_max <= 2^26, else TOR_PREC_DD.  B not positive definite in FP32
  * gives bits_needed = +inf and tier TOR_PREC_DD.  An instance with k
  * outside [0, TOR_MAX_K] or a null matrix gets tier 0 and NaN fields.
  * The estimates are heuristic: on Haar-mixed lossy GBS states kappa_est
@@ -427,7 +429,9 @@ int tor_transform_time(tor_ctx *ctx, float *ms);
  * tor_autotune: pick the chunk depth d (walked modes per chunk k - d) and
  * blocks per SM that run fastest for instances of k clicks in tier `prec`,
  * by timing candidates (k - d in {8, 10, 12, 13, 14, 15, 16}, 2-4 blocks per SM) on a
- * synthetic instance of that size (the walk's cost depends only on k).  The
+ * synthetic instance of that size (the walk's cost depends only on k); each
+ * candidate walks two waves of chunks (or all of them, when fewer) whose
+ * high chunk bits are half set, and its time is scaled to all 2^d.  The
  * choice is kept in the context (used by tor_single when chunk bits are
  * automatic, and by the batch planner for that k) and, if cache_path is not
  * NULL, appended to that file as one JSON object per line keyed by GPU name,
@@ -440,6 +444,12 @@ int tor_autotune(tor_ctx *ctx, int k, int prec, const char *cache_path, int *chu
 /* Measured FP64 FMA throughput of this GPU (DFMA per second), from a
  * dependent-chain-free DFMA loop over all SMs; the roofline denominator. */
 int tor_fp64_peak(tor_ctx *ctx, double *dfma_per_s, double *sm_clock_hz);
+
+/* Measured throughput of the integer multiply-add that the fixed-point tiers
+ * are built on: signed 32 x 32 -> 64-bit multiply-adds (mad.wide.s32) per
+ * second, from independent chains over all SMs; the roofline denominator of
+ * the 256-bit-class tier (whose limb products are exactly these operations). */
+int tor_int_peak(tor_ctx *ctx, double *mad_per_s);
 
 #ifdef __cplusplus
 }

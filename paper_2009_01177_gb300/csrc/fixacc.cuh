@@ -10,8 +10,9 @@
 //
 // The accumulators are L 64-bit limbs with L/2 of them fraction: 256 bits
 // (128 fraction bits) for the FP64, double-double and 128-bit fixed-point
-// tiers, whose terms have no bits below 2^-128, and 384 bits (192 fraction
-// bits) for the 256-bit fixed-point tier, whose terms carry 192 fraction bits.
+// tiers, whose terms have no bits below 2^-128, and 512 bits (256 fraction
+// bits) for the partial sums of the 256-bit-class tier, whose terms carry 203
+// fraction bits (tor_fx9.cuh).
 //
 // Integer adds with carry cost nothing next to the FP64 pipe on sm_103a
 // (about 60 integer ops per clock per SM against 2 DFMA), which is why the
@@ -26,7 +27,7 @@ struct alignas(16) FxW {
   unsigned long long w[L];  // little-endian limbs, value = signed int / 2^(32 L)
 };
 using Fx256 = FxW<4>;  // 128 fraction bits
-using Fx384 = FxW<6>;  // 192 fraction bits
+using Fx512 = FxW<8>;  // 256 fraction bits
 
 template <int L>
 __host__ __device__ __forceinline__ void fx_zero(FxW<L> &a) {
@@ -51,25 +52,31 @@ __device__ __forceinline__ void fx_sub(Fx256 &a, const Fx256 &b) {
       : "+l"(a.w[0]), "+l"(a.w[1]), "+l"(a.w[2]), "+l"(a.w[3])
       : "l"(b.w[0]), "l"(b.w[1]), "l"(b.w[2]), "l"(b.w[3]));
 }
-__device__ __forceinline__ void fx_add(Fx384 &a, const Fx384 &b) {
-  asm("add.cc.u64 %0, %0, %6;\n\t"
-      "addc.cc.u64 %1, %1, %7;\n\t"
-      "addc.cc.u64 %2, %2, %8;\n\t"
-      "addc.cc.u64 %3, %3, %9;\n\t"
-      "addc.cc.u64 %4, %4, %10;\n\t"
-      "addc.u64 %5, %5, %11;"
-      : "+l"(a.w[0]), "+l"(a.w[1]), "+l"(a.w[2]), "+l"(a.w[3]), "+l"(a.w[4]), "+l"(a.w[5])
-      : "l"(b.w[0]), "l"(b.w[1]), "l"(b.w[2]), "l"(b.w[3]), "l"(b.w[4]), "l"(b.w[5]));
+__device__ __forceinline__ void fx_add(Fx512 &a, const Fx512 &b) {
+  asm("add.cc.u64 %0, %0, %8;\n\t"
+      "addc.cc.u64 %1, %1, %9;\n\t"
+      "addc.cc.u64 %2, %2, %10;\n\t"
+      "addc.cc.u64 %3, %3, %11;\n\t"
+      "addc.cc.u64 %4, %4, %12;\n\t"
+      "addc.cc.u64 %5, %5, %13;\n\t"
+      "addc.cc.u64 %6, %6, %14;\n\t"
+      "addc.u64 %7, %7, %15;"
+      : "+l"(a.w[0]), "+l"(a.w[1]), "+l"(a.w[2]), "+l"(a.w[3]), "+l"(a.w[4]), "+l"(a.w[5]), "+l"(a.w[6]),
+        "+l"(a.w[7])
+      : "l"(b.w[0]), "l"(b.w[1]), "l"(b.w[2]), "l"(b.w[3]), "l"(b.w[4]), "l"(b.w[5]), "l"(b.w[6]), "l"(b.w[7]));
 }
-__device__ __forceinline__ void fx_sub(Fx384 &a, const Fx384 &b) {
-  asm("sub.cc.u64 %0, %0, %6;\n\t"
-      "subc.cc.u64 %1, %1, %7;\n\t"
-      "subc.cc.u64 %2, %2, %8;\n\t"
-      "subc.cc.u64 %3, %3, %9;\n\t"
-      "subc.cc.u64 %4, %4, %10;\n\t"
-      "subc.u64 %5, %5, %11;"
-      : "+l"(a.w[0]), "+l"(a.w[1]), "+l"(a.w[2]), "+l"(a.w[3]), "+l"(a.w[4]), "+l"(a.w[5])
-      : "l"(b.w[0]), "l"(b.w[1]), "l"(b.w[2]), "l"(b.w[3]), "l"(b.w[4]), "l"(b.w[5]));
+__device__ __forceinline__ void fx_sub(Fx512 &a, const Fx512 &b) {
+  asm("sub.cc.u64 %0, %0, %8;\n\t"
+      "subc.cc.u64 %1, %1, %9;\n\t"
+      "subc.cc.u64 %2, %2, %10;\n\t"
+      "subc.cc.u64 %3, %3, %11;\n\t"
+      "subc.cc.u64 %4, %4, %12;\n\t"
+      "subc.cc.u64 %5, %5, %13;\n\t"
+      "subc.cc.u64 %6, %6, %14;\n\t"
+      "subc.u64 %7, %7, %15;"
+      : "+l"(a.w[0]), "+l"(a.w[1]), "+l"(a.w[2]), "+l"(a.w[3]), "+l"(a.w[4]), "+l"(a.w[5]), "+l"(a.w[6]),
+        "+l"(a.w[7])
+      : "l"(b.w[0]), "l"(b.w[1]), "l"(b.w[2]), "l"(b.w[3]), "l"(b.w[4]), "l"(b.w[5]), "l"(b.w[6]), "l"(b.w[7]));
 }
 #else
 template <int L>

@@ -15,38 +15,47 @@
 //  k_batch_walk<T>   persistent: each warp takes 32 consecutive items from an
 //                    atomic counter, finds each item's instance by binary search
 //                    over the scan, gathers I - O straight from the caller's
-//                    matrix, walks the chunk (tor_dfs.cuh), and adds the exact
-//                    256-bit partial sums into the instance's accumulator with
-//                    64-bit atomics that propagate carries.  Integer addition
-//                    is associative, so the result does not depend on which
-//                    warp ran which item.
+//                    matrix, walks the chunk (tor_dfs.cuh; tor_fx9.cuh for the
+//                    256-bit-class tier), and adds the exact partial sums
+//                    into the instance's accumulator with 64-bit atomics that
+//                    propagate carries.  Integer addition is associative, so
+//                    the result does not depend on which warp ran which item.
 //  k_batch_finalize  one thread per instance: accumulator -> tor_result.
 //
-// Three tiers share the item axis in the order FP64, double-double, 128-bit
-// fixed point.  In TOR_PREC_AUTO mode up to two more plan/walk/finalize
-// rounds re-run every instance whose result misses the tolerance one tier up:
-// FP64 -> fixed point (when t_max fits its range) or double-double, then
-// fixed point -> double-double.
+// Four tiers share the item axis in the order FP64, double-double, 128-bit
+// fixed point, 256-bit-class fixed point (the per-instance precision choice
+// of Sec. 5.4, Eq. bitlen).  In TOR_PREC_AUTO mode up to two more
+// plan/walk/finalize rounds re-run every instance whose result misses the
+// tolerance in the next tier with more precision whose range holds it:
+// FP64 -> 128-bit -> 256-bit fixed point, double-double only for instances
+// outside the fixed-point ranges.
 #include <cuda_runtime.h>
 #include <cstdint>
 #include "tor_dfs.cuh"
 #include "tor_internal.h"
 #include "tor_walk.cuh"
+#include "tor_fx9.cuh"
 
 namespace tor {
 
 constexpr int PLAN_THREADS = 1024;
-constexpr int NKEY = 3 * 65;  // (tier 1|2|3) x (64 - r1)
+constexpr int NTIER = 4;
+constexpr int NKEY = NTIER * 65;  // (tier 1..4) x (64 - r1)
+constexpr int ACC_LIMBS = 16;     // per instance: two sums of up to 8 limbs
 
 __device__ __forceinline__ bool fx_in_range(const tor_bound &b) {
   return b.log_tmax <= FX128_MAX_LOG2_TMAX * 0.6931472f;
 }
+__device__ __forceinline__ bool fx256_in_range(const tor_bound &b) {
+  return b.log_tmax <= FX256_MAX_LOG2_TMAX * 0.6931472f;
+}
 
-// acc (4 limbs) += X, exactly modulo 2^256, from any number of threads
-__device__ __forceinline__ void fx_atomic_add(unsigned long long *acc, const Fx256 &X) {
+// acc (L limbs) += X, exactly modulo 2^(64 L), from any number of threads
+template <int L>
+__device__ __forceinline__ void fx_atomic_add(unsigned long long *acc, const FxW<L> &X) {
   unsigned long long carry = 0ull;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < L; ++j) {
     const unsigned long long v = X.w[j] + carry;
     const unsigned long long c1 = (v < carry) ? 1ull : 0ull;  // X.w[j] == 2^64-1 with a carry in
     unsigned long long c2 = 0ull;
@@ -58,9 +67,10 @@ __device__ __forceinline__ void fx_atomic_add(unsigned long long *acc, const Fx2
   }
 }
 
-// mode 0: first round; mode 1: escalate the instances that missed tol one tier
-// up (FP64 -> fixed point when in range, else double-double; fixed point ->
-// double-double); bounds is needed for AUTO and for an explicit FX128 batch
+// mode 0: first round; mode 1: escalate the instances that missed tol to the
+// next tier with more precision whose range holds them (FP64 -> 128-bit ->
+// 256-bit fixed point, double-double outside the fixed-point ranges); bounds
+// is needed for AUTO and for explicit fixed-point batches
 __global__ void __launch_bounds__(PLAN_THREADS)
 k_batch_plan(const int *__restrict__ k, const tor_bound *__restrict__ bounds, int n, int prec, int kmax,
              const unsigned char *__restrict__ r1_table /* [4][65] */, int mode, double tol,
@@ -76,9 +86,9 @@ k_batch_plan(const int *__restrict__ k, const tor_bound *__restrict__ bounds, in
     int tier;
     if (mode == 0) {
       tier = (prec == TOR_PREC_AUTO) ? (bounds ? bounds[i].tier : TOR_PREC_FP64) : prec;
-      if (tier == TOR_PREC_FX256) tier = TOR_PREC_DD;  // batches have no 256-bit tier
       if (ki < 0 || ki > kmax) tier = 0;
       if (tier == TOR_PREC_FX128 && ki > 0 && !(bounds && fx_in_range(bounds[i]))) tier = 0;
+      if (tier == TOR_PREC_FX256 && ki > 0 && !(bounds && fx256_in_range(bounds[i]))) tier = 0;
       p.tier[i] = (unsigned char)tier;
       p.flags[i] = (tier == 0) ? ST_RANGE : 0;
       p.escalated[i] = 0;
@@ -87,10 +97,14 @@ k_batch_plan(const int *__restrict__ k, const tor_bound *__restrict__ bounds, in
       const tor_result r = p.result[i];
       const double mag = r.hi < 0 ? -r.hi : r.hi;
       if (r.status == TOR_OK && r.err_est > tol * mag) {
+        const bool f1 = bounds && ki > 0 && fx_in_range(bounds[i]);
+        const bool f2 = bounds && ki > 0 && fx256_in_range(bounds[i]);
         if (p.tier[i] == TOR_PREC_FP64)
-          tier = (bounds && ki > 0 && fx_in_range(bounds[i])) ? TOR_PREC_FX128 : TOR_PREC_DD;
+          tier = f1 ? TOR_PREC_FX128 : (f2 ? TOR_PREC_FX256 : TOR_PREC_DD);
         else if (p.tier[i] == TOR_PREC_FX128)
-          tier = TOR_PREC_DD;
+          tier = f2 ? TOR_PREC_FX256 : TOR_PREC_DD;
+        else if (p.tier[i] == TOR_PREC_DD && f2)
+          tier = TOR_PREC_FX256;
       }
       p.escalated[i] = (tier != 0) ? 1 : 0;
       if (tier != 0) {
@@ -107,10 +121,14 @@ k_batch_plan(const int *__restrict__ k, const tor_bound *__restrict__ bounds, in
     p.r1[i] = (unsigned char)r1;
     p.key[i] = key;
     if (mode == 0 || tier != 0) {
-      unsigned long long *a = p.acc + (size_t)i * 8;
+      unsigned long long *a = p.acc + (size_t)i * ACC_LIMBS;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) a[j] = 0ull;
-      if (ki == 0 && tier != 0) { a[2] = 1ull; a[6] = 1ull; }  // Tor = sum t = 1 (empty set only)
+      for (int j = 0; j < ACC_LIMBS; ++j) a[j] = 0ull;
+      if (ki == 0 && tier != 0) {  // Tor = sum t = 1 (empty set only): 1 in the tier's sums
+        const int L = partial_limbs(tier) / 2;
+        a[L / 2] = 1ull;
+        a[L + L / 2] = 1ull;
+      }
     }
     if (key >= 0) atomicAdd(&hist[key], 1u);
   }
@@ -131,7 +149,7 @@ k_batch_plan(const int *__restrict__ k, const tor_bound *__restrict__ bounds, in
   }
   __syncthreads();
   // phase 3: exclusive scan of chunk counts over the sorted order
-  const int m = (int)p.counts[2];
+  const int m = (int)p.counts[NTIER - 1];
   const int per = (m + PLAN_THREADS - 1) / PLAN_THREADS;
   const int lo = tid * per, hi = min(m, lo + per);
   unsigned long long sum = 0;
@@ -157,7 +175,7 @@ k_batch_plan(const int *__restrict__ k, const tor_bound *__restrict__ bounds, in
   if (tid == PLAN_THREADS - 1) p.item_off[m] = run;
   __syncthreads();
   if (tid == 0) {  // items of tier t + 1: [range[2t], range[2t + 1])
-    for (int t = 0; t < 3; ++t) {
+    for (int t = 0; t < NTIER; ++t) {
       p.range[2 * t] = (t == 0) ? 0ull : p.item_off[p.counts[t - 1]];
       p.range[2 * t + 1] = p.item_off[p.counts[t]];
       p.counter[t] = p.range[2 * t];
@@ -210,11 +228,70 @@ k_batch_walk(BatchInput in, BatchPlan p, double *__restrict__ scratch) {
         const SrcDirect src{in.O[i], ki, in.ld[i], in.layout};
         walk_chunk<Tier>(src, ki, r1, c, S, st, Sm, Q, blockDim.x);
       }
-      fx_atomic_add(p.acc + (size_t)i * 8, Sm.tor);
-      fx_atomic_add(p.acc + (size_t)i * 8 + 4, Sm.sabs);
+      fx_atomic_add(p.acc + (size_t)i * ACC_LIMBS, Sm.tor);
+      fx_atomic_add(p.acc + (size_t)i * ACC_LIMBS + 4, Sm.sabs);
       if (Sm.flags) atomicOr(p.flags + i, Sm.flags);
     }
   }
+}
+
+// The 256-bit-class tier's persistent walk: the same item scheme, the fx9
+// walk (tor_fx9.cuh) with its planar global stacks and shared-memory
+// mini-stacks, 512-bit partial sums.
+template <bool PAT>
+__global__ void __launch_bounds__(128, FX9_MINB)
+k_batch_walk_fx9(BatchInput in, BatchPlan p, char *__restrict__ scratch) {
+  extern __shared__ int4 smem_b9[];
+  constexpr int t = TOR_PREC_FX256 - 1;
+  const unsigned st = gridDim.x * blockDim.x;
+  const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const Fx9Mem G{scratch, st, gtid};
+  const Fx9Mem Q{reinterpret_cast<char *>(smem_b9), blockDim.x, threadIdx.x};
+  const int lane = threadIdx.x & 31;
+  const unsigned long long end = p.range[2 * t + 1];
+  const int jlo = (int)p.counts[t - 1];
+  const int jhi = (int)p.counts[t];
+  while (true) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(p.counter + t, 32ull);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (base >= end) break;
+    const unsigned long long item = base + lane;
+    if (item < end) {
+      int a = jlo, b = jhi - 1;
+      while (a < b) {
+        const int mid = (a + b + 1) >> 1;
+        if (p.item_off[mid] <= item) a = mid; else b = mid - 1;
+      }
+      const int i = p.order[a];
+      const unsigned long long c = item - p.item_off[a];
+      const int ki = in.k[i], r1 = p.r1[i];
+      Fx9Sums A;
+      A.zero();
+      if constexpr (PAT) {
+        unsigned char gm[64];
+        int m = 0;
+        for (int w = 0; w < in.words; ++w)
+          for (unsigned long long bits = in.patterns[(size_t)i * in.words + w]; bits && m < 64; bits &= bits - 1)
+            gm[m++] = (unsigned char)(64 * w + __ffsll((long long)bits) - 1);
+        const SrcPattern src{in.Ofull, in.M, in.ldfull, gm};
+        fx9_walk_chunk(src, ki, r1, c, G, Q, A);
+      } else {
+        const SrcDirect src{in.O[i], ki, in.ld[i], in.layout};
+        fx9_walk_chunk(src, ki, r1, c, G, Q, A);
+      }
+      Fx512 ct, cs;
+      fx9_fold(A, ct, cs);
+      fx_atomic_add(p.acc + (size_t)i * ACC_LIMBS, ct);
+      fx_atomic_add(p.acc + (size_t)i * ACC_LIMBS + 8, cs);
+      if (A.flags) atomicOr(p.flags + i, A.flags);
+    }
+  }
+}
+
+static size_t fx9_batch_smem(int block) {
+  const size_t slot = (size_t)fx9_smem_entries(FX9_RSMEM) * 36;
+  return slot * (size_t)block;
 }
 
 // tol > 0: mark results whose error bound exceeds tol * |Tor| with TOR_EPREC
@@ -227,7 +304,7 @@ __global__ void k_batch_finalize(const int *__restrict__ k, int n, int only_esca
   if (p.tier[i] == 0) {
     r = tor_result{0.0, 0.0, 0.0, 0.0, 0, TOR_EINVAL};
   } else {
-    fixed_to_result(p.acc + (size_t)i * 8, k[i], p.tier[i], p.flags[i], &r);
+    fixed_to_result(p.acc + (size_t)i * ACC_LIMBS, k[i], p.tier[i], p.flags[i], &r);
     const double mag = r.hi < 0 ? -r.hi : r.hi;
     if (tol > 0.0 && r.status == TOR_OK && r.err_est > tol * mag) r.status = TOR_EPREC;
   }
@@ -244,7 +321,17 @@ int launch_batch_plan(const int *k, const tor_bound *bounds, int n, int prec, in
 int launch_batch_walk(int tier, int grid, int block, const BatchInput &in, const BatchPlan &p, double *scratch,
                       cudaStream_t s) {
   const bool pat = in.words > 0;
-  if (tier == TOR_PREC_DD) {
+  if (tier == TOR_PREC_FX256) {
+    const size_t sm = fx9_batch_smem(block);
+    char *scr = reinterpret_cast<char *>(scratch);
+    if (pat) {
+      cudaFuncSetAttribute(k_batch_walk_fx9<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_batch_walk_fx9<true><<<grid, block, sm, s>>>(in, p, scr);
+    } else {
+      cudaFuncSetAttribute(k_batch_walk_fx9<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_batch_walk_fx9<false><<<grid, block, sm, s>>>(in, p, scr);
+    }
+  } else if (tier == TOR_PREC_DD) {
     const size_t sm = walk_smem_bytes<TierDD>(block);
     if (pat) k_batch_walk<TierDD, true><<<grid, block, sm, s>>>(in, p, scratch);
     else k_batch_walk<TierDD, false><<<grid, block, sm, s>>>(in, p, scratch);
@@ -290,6 +377,10 @@ static int occ_of(K kern, int block, size_t sm) {
 }
 
 int batch_walk_max_blocks_per_sm(int tier, int block, bool patterns) {
+  if (tier == TOR_PREC_FX256) {
+    const size_t sm = fx9_batch_smem(block);
+    return patterns ? occ_of(k_batch_walk_fx9<true>, block, sm) : occ_of(k_batch_walk_fx9<false>, block, sm);
+  }
   if (tier == TOR_PREC_FX128) {
     using TF = TierFx<FX128_FRAC>;
     const size_t sm = walk_smem_bytes<TF>(block);

@@ -122,11 +122,11 @@ __device__ void bounds_one(const Get &getO, bool valid, int k, double tol, float
                        (float)log2(1.0 / (tol > 0 ? tol : 1e-300));
     bd.bits_needed = s_bad ? INFINITY : bits;
     const bool fx_ok = !s_bad && bd.log_tmax <= FX128_MAX_LOG2_TMAX * 0.6931472f;
-    const bool fx4_ok = !s_bad && bd.log_tmax <= FX256_MAX_LOG2_TMAX * 0.6931472f;
+    const bool fx256_ok = !s_bad && bd.log_tmax <= FX256_MAX_LOG2_TMAX * 0.6931472f;
     bd.tier = (!s_bad && bits <= FP64_ROUTE_BITS)            ? TOR_PREC_FP64
               : (fx_ok && bits <= FX128_ROUTE_BITS)           ? TOR_PREC_FX128
               : (!s_bad && bits <= DD_ROUTE_BITS)             ? TOR_PREC_DD
-              : fx4_ok                                        ? TOR_PREC_FX256
+              : fx256_ok                                        ? TOR_PREC_FX256
                                                               : TOR_PREC_DD;
     *out = bd;
   }

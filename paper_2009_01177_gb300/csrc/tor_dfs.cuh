@@ -47,7 +47,6 @@
 #include "fixacc.cuh"
 #include "dd.cuh"
 #include "fx128.cuh"
-#include "fx256.cuh"
 
 namespace tor {
 
@@ -130,19 +129,6 @@ __device__ __forceinline__ void fx_add_signed(Fx256 &acc, double x, bool neg, in
 #ifndef TOR_FX_MINB
 #define TOR_FX_MINB 4
 #endif
-// The 256-bit tier: values are eight registers, so one-mode register subtrees,
-// small shared-memory nodes (four doubles per entry), and three resident
-// blocks (168 registers, some spills): 14% faster than two at k = 28.
-#ifndef TOR_FX4_RREG
-#define TOR_FX4_RREG 1
-#endif
-#ifndef TOR_FX4_RSMEM
-#define TOR_FX4_RSMEM 2
-#endif
-#ifndef TOR_FX4_MINB
-#define TOR_FX4_MINB 3
-#endif
-
 __device__ __forceinline__ double dmul(double a, double b) { return a * b; }
 
 // 1/sqrt(x) for a positive double x, accurate to about one ulp.
@@ -398,116 +384,6 @@ struct TierFx {
     X.w[1] = (sh == 64) ? t.lo : ((hi << sh) | (t.lo >> (64 - sh)));
     X.w[2] = (sh == 64) ? hi : (hi >> (64 - sh));
     X.w[3] = 0ull;
-    if (neg) fx_sub(S.tor, X); else fx_add(S.tor, X);
-    fx_add(S.sabs, X);
-  }
-};
-
-// ------------------------------------------------- 256-bit fixed-point tier
-// The paper's 256-bit mode (Sec. 5.1-5.2): 256-bit two's-complement integers
-// with 192 fraction bits (fx256.cuh), four doubles per stored entry.  Every
-// intermediate must stay below 2^63; the largest are the pivot inverses
-// 1/det2 <= t_max^2, so instances need t_max <= 2^30.  The terms carry 192
-// fraction bits, so they go to 384-bit accumulators (192 fraction bits).
-struct TierFx4 {
-  using T = fx4;
-  using Acc = Fx384;
-  static constexpr int W = 4;
-  static constexpr int RREG = TOR_FX4_RREG;
-  static constexpr int RUNROLL = 0;
-  static constexpr int RSMEM = TOR_FX4_RSMEM;
-  static constexpr int MINB = TOR_FX4_MINB;
-  static constexpr int PREC = 4;  // TOR_PREC_FX256
-
-  __device__ static __forceinline__ T ld(const double *P, int e, size_t st) {
-    T v;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) v.w[i] = (unsigned long long)__double_as_longlong(P[(size_t)(4 * e + i) * st]);
-    return v;
-  }
-  __device__ static __forceinline__ void stv(double *P, int e, size_t st, T v) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) P[(size_t)(4 * e + i) * st] = __longlong_as_double((long long)v.w[i]);
-  }
-  __device__ static __forceinline__ T one() { return {{0ull, 0ull, 0ull, 1ull}}; }
-  // exact for 2^-139 <= |x| < 2^10 (53 mantissa bits at or above 2^-192);
-  // smaller magnitudes lose their low bits, larger ones set ST_RANGE
-  __device__ static __forceinline__ T from_double(double x, int &fl) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-    const int e = (int)((bits >> 52) & 0x7FF);
-    T r = {{0ull, 0ull, 0ull, 0ull}};
-    if (e == 0) return r;
-    const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
-    const int sh = e - 1075 + FX256_FRAC;  // value = m 2^sh in units of 2^-192
-    if (sh < 0) {
-      r.w[0] = (sh > -64) ? (m >> (-sh)) : 0ull;
-    } else if (sh + 53 > 255) {
-      fl |= ST_RANGE;
-    } else {
-      const int q = sh >> 6, sb = sh & 63;
-      const unsigned long long lo = m << sb, hi = sb ? (m >> (64 - sb)) : 0ull;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) r.w[i] = (q == i) ? lo : ((q + 1 == i) ? hi : 0ull);
-    }
-    return (bits >> 63) ? fx4_neg(r) : r;
-  }
-  __device__ static __forceinline__ double to_double(const T &x) {
-    const bool neg = fx4_neg_p(x);
-    const T m = neg ? fx4_neg(x) : x;
-    const double d = (double)m.w[3] + (double)m.w[2] * 0x1p-64 + (double)m.w[1] * 0x1p-128;
-    return neg ? -d : d;
-  }
-  __device__ static __forceinline__ T from_hilo(double h, double l) {
-    int fl = 0;
-    return fx4_add(from_double(h, fl), from_double(l, fl));
-  }
-  __device__ static __forceinline__ T from_o(double o, bool diag) {
-    int fl = 0;
-    const T v = from_double(o, fl);
-    return diag ? fx4_sub(one(), v) : fx4_neg(v);
-  }
-  __device__ static __forceinline__ T mul(T a, T b, int &fl) {
-    int o = 0;
-    const T r = fx4_mul(a, b, o);
-    if (o) fl |= ST_RANGE;
-    return r;
-  }
-  __device__ static __forceinline__ T det2(T a, T b, T d, int &fl) { return fx4_sub(mul(a, d, fl), mul(b, b, fl)); }
-  __device__ static __forceinline__ bool bad(T x) {
-    return fx4_neg_p(x) || ((x.w[0] | x.w[1] | x.w[2] | x.w[3]) == 0ull);
-  }
-  // 1/sqrt(x): an FP64 seed (about 52 bits) and two fixed-point Newton steps
-  // y <- y (3 - x y^2) / 2, which take it past the 192 fraction bits
-  __device__ static __forceinline__ T rsqrt(T x, int &fl) {
-    const double xd = to_double(x);
-    T y = from_double(xd > 0.0 ? rsqrt_fp64(xd) : 0.0, fl);
-    const T three = {{0ull, 0ull, 0ull, 3ull}};
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-      const T e = fx4_sub(three, mul(x, mul(y, y, fl), fl));
-      const T p = mul(y, e, fl);
-      y.w[0] = (p.w[0] >> 1) | (p.w[1] << 63);  // / 2 (arithmetic shift)
-      y.w[1] = (p.w[1] >> 1) | (p.w[2] << 63);
-      y.w[2] = (p.w[2] >> 1) | (p.w[3] << 63);
-      y.w[3] = (unsigned long long)((long long)p.w[3] >> 1);
-    }
-    return y;
-  }
-  __device__ static __forceinline__ void coef(T a, T b, T d, T y, T &al, T &be, T &de, int &fl) {
-    const T inv = mul(y, y, fl);
-    al = mul(d, inv, fl); be = mul(b, inv, fl); de = mul(a, inv, fl);
-  }
-  __device__ static __forceinline__ void vrow(T al, T be, T de, T ux, T up, T &vx, T &vp, int &fl) {
-    vx = fx4_sub(mul(al, ux, fl), mul(be, up, fl));
-    vp = fx4_sub(mul(de, up, fl), mul(be, ux, fl));
-  }
-  __device__ static __forceinline__ T upd(T s, T vx, T ux, T vp, T up, int &fl) {
-    return fx4_sub(fx4_sub(s, mul(vx, ux, fl)), mul(vp, up, fl));
-  }
-  // t (192 fraction bits, positive) into the 192-fraction-bit accumulators, exactly
-  __device__ static __forceinline__ void acc(SumsOf<Fx384> &S, T t, bool neg) {
-    if (fx4_neg_p(t)) { S.flags |= ST_RANGE; return; }
-    const Fx384 X = {{t.w[0], t.w[1], t.w[2], t.w[3], 0ull, 0ull}};
     if (neg) fx_sub(S.tor, X); else fx_add(S.tor, X);
     fx_add(S.sabs, X);
   }

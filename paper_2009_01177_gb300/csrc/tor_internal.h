@@ -12,33 +12,38 @@ namespace tor {
 // error of the Schur updates; gamma = 4k covers those with margin.
 __host__ __device__ inline double err_gamma(int k) { return 4.0 * (k > 1 ? k : 1); }
 // fixed point: absolute rounding 2^-104 per product, relative 2^-100 for the
-// values >= 1/16 the walk carries (Schur entries, pivots, terms); 256-bit:
-// 2^-192 per product plus at most a few units of dropped carries, 2^-186
+// values >= 1/16 the walk carries (Schur entries, pivots, terms); 256-bit
+// class (nine 29-bit limbs, 203 fraction bits): at most 3.5 units of 2^-203
+// per product or fused two-product operation, under 2^-197 relative on values
+// >= 1/16, 2^-196 with margin
 __host__ __device__ inline double unit_roundoff(int tier) {
   return tier == TOR_PREC_DD      ? 0x1p-104
          : tier == TOR_PREC_FX128 ? 0x1p-100
-         : tier == TOR_PREC_FX256 ? 0x1p-186
+         : tier == TOR_PREC_FX256 ? 0x1p-196
                                   : 0x1p-53;
 }
 constexpr int FX128_FRAC = 104;
 // largest log2 t_max for which every intermediate fits: 2 log2 t_max < 127 - F - 1
 constexpr float FX128_MAX_LOG2_TMAX = 11.0f;
-// the same for the 256-bit tier: 2 log2 t_max < 255 - 192 - 1
-constexpr float FX256_MAX_LOG2_TMAX = 30.0f;
+// the 256-bit-class tier holds magnitudes below 2^57; the pivot inverses reach
+// t_max^2 and the Schur coefficients D^-1 u a few times that, so t_max <= 2^26
+constexpr float FX256_MAX_LOG2_TMAX = 26.0f;
+// walked modes per fx9 chunk: its 64-bit column sums take at most 2^34 terms
+constexpr int FX256_MAX_R1 = 34;
 
 // device arrays of a batch plan (sized for n_max instances by tor_batch_reserve)
 struct BatchPlan {
-  unsigned char *tier;            // n: 0 = not scheduled (invalid), else TOR_PREC_FP64 | DD | FX128
+  unsigned char *tier;            // n: 0 = not scheduled (invalid), else TOR_PREC_FP64 | DD | FX128 | FX256
   unsigned char *r1;              // n: walked (low) modes per chunk
   unsigned char *escalated;       // n: re-run one tier up by the current AUTO round
   int *key;                       // n: sort key, -1 = not scheduled
   int *order;                     // n: instances sorted by (tier, r1 descending)
   int *flags;                     // n: ST_* status bits
   unsigned long long *item_off;   // n + 1: exclusive scan of chunk counts in sorted order
-  unsigned long long *acc;        // n x 8: exact fixed-point sums (signed, abs)
-  unsigned long long *range;      // 6: [begin, end) item range of each tier (FP64, DD, FX128)
-  unsigned long long *counter;    // 3: work counter of each tier
-  unsigned int *counts;           // 3: scheduled instances of tiers <= FP64, <= DD, <= FX128
+  unsigned long long *acc;        // n x 16: exact fixed-point sums (signed, abs; 4 or 8 limbs each)
+  unsigned long long *range;      // 8: [begin, end) item range of each tier (FP64, DD, FX128, FX256)
+  unsigned long long *counter;    // 4: work counter of each tier
+  unsigned int *counts;           // 4: scheduled instances of tiers <= FP64, <= DD, <= FX128, <= FX256
   tor_result *result;             // n: last finalized results (input of the AUTO round)
 };
 
@@ -83,6 +88,9 @@ void launch_dfs(int tier, int grid, int block, const double *B, const double *Bl
 void launch_finalize(const unsigned long long *block_part, int nblocks, int k, int tier,
                      const int *status, tor_result *out, cudaStream_t s);
 void launch_dfma_peak(double *sink, int grid, int block, int iters, cudaStream_t s);
+void launch_imad_peak(long long *sink, int grid, int block, int iters, cudaStream_t s);
+// writes Tor = 1 (the k = 0 result) of tier `tier` to out, on the stream
+int launch_result_one(tor_result *out, int tier, cudaStream_t s);
 // all-pattern tables (tor_table.cu)
 int table_walk_max_blocks_per_sm(int tier, int block);
 int launch_table_walk(int tier, int grid, int block, const double *B, const double *Blo, int k, int r1,
@@ -90,8 +98,8 @@ int launch_table_walk(int tier, int grid, int block, const double *B, const doub
 int launch_table_transform(Fx256 *t, double *s, int M, cudaStream_t st);
 int launch_table_finalize(const Fx256 *t, const double *s, int M, int tier, const int *status, tor_result *out,
                           cudaStream_t st);
-int launch_fx256_mul(const unsigned long long *a, const unsigned long long *b, int n, unsigned long long *out,
-                     int *ovf, cudaStream_t s);
+int launch_fx256_fma2(const int *s, const int *a1, const int *b1, const int *a2, const int *b2, int n, int *out,
+                      int *ovf, cudaStream_t st);
 int scratch_entries(int tier, int k, int r1);
 int dfs_max_blocks_per_sm(int tier, int block);
 int launch_bounds_batch(const double *const *O, const int *k, const int *ld, int n, int layout, double tol,

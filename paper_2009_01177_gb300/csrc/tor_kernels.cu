@@ -13,6 +13,7 @@
 #include "tor_dfs.cuh"
 #include "tor_internal.h"
 #include "tor_walk.cuh"
+#include "tor_fx9.cuh"
 
 namespace tor {
 
@@ -99,6 +100,72 @@ k_dfs(const double *__restrict__ B, const double *__restrict__ Blo, int k, const
   }
 }
 
+// The 256-bit-class tier: the fx9 walk (tor_fx9.cuh) over the same chunk
+// segments; per-thread 512-bit totals, exact block sums of 16 limbs.
+__global__ void __launch_bounds__(128, FX9_MINB)
+k_dfs_fx9(const double *__restrict__ B, const double *__restrict__ Blo, int k, const WalkSegs seg,
+          char *__restrict__ scratch, unsigned long long *__restrict__ block_part,
+          unsigned long long *__restrict__ chunk_part, int *__restrict__ status) {
+  extern __shared__ int4 smem_fx9[];
+  const unsigned st = gridDim.x * blockDim.x;
+  const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const Fx9Mem G{scratch, st, gtid};
+  const Fx9Mem Q{reinterpret_cast<char *>(smem_fx9), blockDim.x, threadIdx.x};
+  const SrcPrepped src{B, Blo, 2 * k};
+  Fx512 tot_tor, tot_sabs;
+  fx_zero(tot_tor);
+  fx_zero(tot_sabs);
+  int flags = 0;
+#pragma unroll 1
+  for (int g = 0; g < 2; ++g) {
+    const int r1 = seg.r1[g];
+#pragma unroll 1
+    for (unsigned long long c = seg.c0[g] + gtid; c < seg.c1[g]; c += st) {
+      Fx9Sums A;
+      A.zero();
+      fx9_walk_chunk(src, k, r1, c, G, Q, A);
+      Fx512 ct, cs;
+      fx9_fold(A, ct, cs);
+      if (chunk_part && g == 0) {
+        unsigned long long *o = chunk_part + (size_t)(c - seg.c0[0]) * 16;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) { o[i] = ct.w[i]; o[8 + i] = cs.w[i]; }
+      }
+      fx_add(tot_tor, ct);
+      fx_add(tot_sabs, cs);
+      flags |= A.flags;
+    }
+  }
+  __syncthreads();
+  unsigned long long(*red)[16] = reinterpret_cast<unsigned long long(*)[16]>(smem_fx9);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) { red[threadIdx.x][i] = tot_tor.w[i]; red[threadIdx.x][8 + i] = tot_sabs.w[i]; }
+  if (flags) atomicOr(status, flags);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Fx512 a, b, x;
+    fx_zero(a);
+    fx_zero(b);
+    for (int t2 = 0; t2 < (int)blockDim.x; ++t2) {
+      for (int i = 0; i < 8; ++i) x.w[i] = red[t2][i];
+      fx_add(a, x);
+      for (int i = 0; i < 8; ++i) x.w[i] = red[t2][8 + i];
+      fx_add(b, x);
+    }
+    for (int i = 0; i < 8; ++i) {
+      block_part[(size_t)blockIdx.x * 16 + i] = a.w[i];
+      block_part[(size_t)blockIdx.x * 16 + 8 + i] = b.w[i];
+    }
+  }
+}
+
+// shared memory of a fx9 walk block: the per-thread mini-stacks (at least the
+// reduction's 128 bytes per thread)
+static size_t fx9_smem_bytes(int block) {
+  const size_t slot = (size_t)fx9_smem_entries(FX9_RSMEM) * 36;
+  return (slot > 128 ? slot : 128) * (size_t)block;
+}
+
 // sum of the blocks' partials (2 L limbs each) -> tor_result
 template <int L>
 __global__ void k_finalize(const unsigned long long *__restrict__ block_part, int nblocks, int k,
@@ -118,6 +185,16 @@ __global__ void k_finalize(const unsigned long long *__restrict__ block_part, in
   fixed_to_result_w<L>(w, k, tier, *status, out);
 }
 
+// Tor of the empty pattern (k = 0): only the empty subset, t = 1
+__global__ void k_result_one(tor_result *out, int tier) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = tor_result{1.0, 0.0, 1.0, 0.0, tier, TOR_OK};
+}
+
+int launch_result_one(tor_result *out, int tier, cudaStream_t s) {
+  k_result_one<<<1, 32, 0, s>>>(out, tier);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 // Independent DFMA chains; the result is consumed so the loop is not removed.
 __global__ void k_dfma_peak(double *sink, int iters, double a, double b) {
   double x0 = threadIdx.x * 1e-9, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3;
@@ -128,30 +205,55 @@ __global__ void k_dfma_peak(double *sink, int iters, double a, double b) {
   if (s == 1234.5) sink[threadIdx.x] = s;
 }
 
+// Independent mad.wide.s32 chains (32 x 32 -> 64 multiply-add, the fixed-point
+// tiers' limb product); the result is consumed so the loop is not removed.
+__global__ void k_imad_peak(long long *sink, int iters, int a, int b) {
+  long long x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = threadIdx.x + j;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) asm volatile("mad.wide.s32 %0, %1, %2, %0;" : "+l"(x[j]) : "r"(a + j), "r"(b));
+  }
+  long long s = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += x[j];
+  if (s == 12345) sink[threadIdx.x] = s;
+}
+
+void launch_imad_peak(long long *sink, int grid, int block, int iters, cudaStream_t s) {
+  k_imad_peak<<<grid, block, 0, s>>>(sink, iters, 3, 5);
+}
+
 // ------------------------------------------------------------ host launchers
 void launch_prep(const double *O, int k, int ld, int layout, double *B, double *Blo, cudaStream_t s) {
   const int n = 4 * k * k;
   k_prep<<<(n + 255) / 256, 256, 0, s>>>(O, k, ld, layout, B, Blo);
 }
 
-// elementwise 256-bit fixed-point products, as the 256-bit tier computes them
-__global__ void k_fx256_mul(const unsigned long long *__restrict__ a, const unsigned long long *__restrict__ b,
-                            int n, unsigned long long *__restrict__ out, int *__restrict__ ovf) {
+// elementwise s + a1 b1 + a2 b2 in the 256-bit-class arithmetic (fx9), as the
+// walk's Schur updates form them; operands of nine int32 limbs each
+__global__ void k_fx256_fma2(const int *__restrict__ s, const int *__restrict__ a1, const int *__restrict__ b1,
+                             const int *__restrict__ a2, const int *__restrict__ b2, int n, int *__restrict__ out,
+                             int *__restrict__ ovf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  fx4 x, y;
+  fx9 v[5];
+  const int *src[5] = {s, a1, b1, a2, b2};
 #pragma unroll
-  for (int j = 0; j < 4; ++j) { x.w[j] = a[4 * (size_t)i + j]; y.w[j] = b[4 * (size_t)i + j]; }
+  for (int q = 0; q < 5; ++q)
+#pragma unroll
+    for (int j = 0; j < 9; ++j) v[q].l[j] = src[q][9 * (size_t)i + j];
   int o = 0;
-  const fx4 r = fx4_mul(x, y, o);
+  const fx9 r = fx9_fma2(v[0], v[1], v[2], v[3], v[4], o);
 #pragma unroll
-  for (int j = 0; j < 4; ++j) out[4 * (size_t)i + j] = r.w[j];
+  for (int j = 0; j < 9; ++j) out[9 * (size_t)i + j] = r.l[j];
   ovf[i] = o;
 }
 
-int launch_fx256_mul(const unsigned long long *a, const unsigned long long *b, int n, unsigned long long *out,
-                     int *ovf, cudaStream_t s) {
-  if (n > 0) k_fx256_mul<<<(n + 127) / 128, 128, 0, s>>>(a, b, n, out, ovf);
+int launch_fx256_fma2(const int *s, const int *a1, const int *b1, const int *a2, const int *b2, int n, int *out,
+                      int *ovf, cudaStream_t st) {
+  if (n > 0) k_fx256_fma2<<<(n + 127) / 128, 128, 0, st>>>(s, a1, b1, a2, b2, n, out, ovf);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -161,7 +263,6 @@ static void with_tier(int tier, F &&f) {
   switch (tier) {
     case TOR_PREC_DD: f(TierDD{}); break;
     case TOR_PREC_FX128: f(TierFx<FX128_FRAC>{}); break;
-    case TOR_PREC_FX256: f(TierFx4{}); break;
     default: f(TierF64{}); break;
   }
 }
@@ -169,6 +270,13 @@ static void with_tier(int tier, F &&f) {
 void launch_dfs(int tier, int grid, int block, const double *B, const double *Blo, int k, const WalkSegs &seg,
                 double *scratch, unsigned long long *block_part, unsigned long long *chunk_part, int *status,
                 cudaStream_t s) {
+  if (tier == TOR_PREC_FX256) {
+    const size_t sm = fx9_smem_bytes(block);
+    cudaFuncSetAttribute(k_dfs_fx9, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_dfs_fx9<<<grid, block, sm, s>>>(B, Blo, k, seg, reinterpret_cast<char *>(scratch), block_part, chunk_part,
+                                       status);
+    return;
+  }
   with_tier(tier, [&](auto t) {
     using Tier = decltype(t);
     const size_t sm = walk_smem_bytes<Tier>(block);
@@ -180,6 +288,12 @@ void launch_dfs(int tier, int grid, int block, const double *B, const double *Bl
 int dfs_max_blocks_per_sm(int tier, int block) {
   int n = 0;
   cudaError_t e = cudaSuccess;
+  if (tier == TOR_PREC_FX256) {
+    const size_t sm = fx9_smem_bytes(block);
+    cudaFuncSetAttribute(k_dfs_fx9, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dfs_fx9, block, sm);
+    return (e == cudaSuccess && n > 0) ? n : 1;
+  }
   with_tier(tier, [&](auto t) {
     using Tier = decltype(t);
     const size_t sm = walk_smem_bytes<Tier>(block);
@@ -191,7 +305,7 @@ int dfs_max_blocks_per_sm(int tier, int block) {
 
 void launch_finalize(const unsigned long long *block_part, int nblocks, int k, int tier,
                      const int *status, tor_result *out, cudaStream_t s) {
-  if (tier == TOR_PREC_FX256) k_finalize<6><<<1, 32, 0, s>>>(block_part, nblocks, k, tier, status, out);
+  if (tier == TOR_PREC_FX256) k_finalize<8><<<1, 32, 0, s>>>(block_part, nblocks, k, tier, status, out);
   else k_finalize<4><<<1, 32, 0, s>>>(block_part, nblocks, k, tier, status, out);
 }
 
@@ -200,6 +314,7 @@ void launch_dfma_peak(double *sink, int grid, int block, int iters, cudaStream_t
 }
 
 int scratch_entries(int tier, int k, int r1) {
+  if (tier == TOR_PREC_FX256) return (fx9_stack_entries(k, r1) * 36 + 7) / 8;  // in doubles
   int rreg = 0, w = 1;
   with_tier(tier, [&](auto t) {
     using Tier = decltype(t);

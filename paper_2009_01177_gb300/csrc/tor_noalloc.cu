@@ -87,12 +87,10 @@ int tor_single_noalloc(const double *O, int k, int ld, int layout, int prec, cud
     base = (unsigned char *)g_noalloc_base[dev];
   }
 
-  if (k == 0) {
-    // Tor = 1 (only the empty set): a constant record is copied to the output.
-    const tor_result one = {1.0, 0.0, 1.0, 0.0, prec, TOR_OK};
-    e = cudaMemcpyAsync(out_dev, &one, sizeof(one), cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // `one` lives on this stack frame
-    return e == cudaSuccess ? TOR_OK : nfail(TOR_ECUDA, "k = 0 result copy: %s", cudaGetErrorString(e));
+  if (k == 0) {  // Tor = 1 (only the empty set), written by a one-thread kernel: stays asynchronous
+    if (tor::launch_result_one(out_dev, prec, stream))
+      return nfail(TOR_ECUDA, "k = 0 result: %s", cudaGetErrorString(cudaGetLastError()));
+    return TOR_OK;
   }
 
   // chunks of at most 10 walked modes (up to 2^18 chunks): short per-thread

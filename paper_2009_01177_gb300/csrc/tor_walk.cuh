@@ -104,13 +104,13 @@ __host__ __device__ inline void fixed_to_result_w(const unsigned long long *w, i
   out->status = (status & ST_NOTPD) ? TOR_ENOTPD : ((status & ST_RANGE) ? TOR_EINVAL : TOR_OK);
 }
 
-// limbs of one partial (signed sum and sum_abs) for a tier: 8, or 12 for the
-// 256-bit fixed-point tier
-__host__ __device__ inline int partial_limbs(int tier) { return tier == TOR_PREC_FX256 ? 12 : 8; }
+// limbs of one partial (signed sum and sum_abs) for a tier: 8 (256-bit sums,
+// 128 fraction bits), or 16 for the 256-bit-class tier (512-bit sums, 256)
+__host__ __device__ inline int partial_limbs(int tier) { return tier == TOR_PREC_FX256 ? 16 : 8; }
 
 __host__ __device__ inline void fixed_to_result(const unsigned long long *w, int k, int tier, int status,
                                                 tor_result *out) {
-  if (tier == TOR_PREC_FX256) fixed_to_result_w<6>(w, k, tier, status, out);
+  if (tier == TOR_PREC_FX256) fixed_to_result_w<8>(w, k, tier, status, out);
   else fixed_to_result_w<4>(w, k, tier, status, out);
 }
 

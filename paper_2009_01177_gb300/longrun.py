@@ -37,7 +37,7 @@ class RunState:
     key: str
     chunk_bits: int
     window: int
-    limbs: int                       # 8, or 12 for the 256-bit tier
+    limbs: int                       # 8, or 16 for the 256-bit tier
     done: np.ndarray                 # bool per window
     total: np.ndarray                # exact partial sum of the finished windows (uint64 limbs)
     seconds: float = 0.0             # wall time spent in finished windows

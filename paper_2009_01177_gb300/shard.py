@@ -3,7 +3,7 @@
 The 2^d prefix chunks are independent and equal in cost (the paper's
 balanced partition, Algorithm 1), so rank r of R evaluates the contiguous
 chunk range [r 2^d / R, (r+1) 2^d / R) with tor_chunks and the ranks exchange
-one fixed-point pair each (256-bit, or 384-bit for the 256-bit fixed-point
+one fixed-point pair each (256-bit, or 512-bit for the 256-bit fixed-point
 tier).  Those partials add exactly (integer addition), so the gathered total
 is bit-identical to a single-GPU run.  The exchange is the only collective; it
 moves 64 (or 96) bytes per rank.
@@ -23,7 +23,7 @@ def chunk_range(rank: int, world: int, nchunks: int):
 
 def limbs_to_ints(limbs):
     """(signed sum, sum_abs) as Python integers modulo 2^(64 L) from 2 L little-endian 64-bit
-    limbs (L = 4, or 6 for the 256-bit fixed-point tier)."""
+    limbs (L = 4, or 8 for the 256-bit fixed-point tier)."""
     a = [int(x) & 0xFFFFFFFFFFFFFFFF for x in np.asarray(limbs).ravel()]
     L = len(a) // 2
     lo = sum(a[i] << (64 * i) for i in range(L))
@@ -44,7 +44,7 @@ def ints_to_limbs(lo: int, hi: int, limbs: int = 8) -> np.ndarray:
 
 
 def sum_partials(rows) -> np.ndarray:
-    """Exact sum of several partials (rows of an (n, 8) or (n, 12) array)."""
+    """Exact sum of several partials (rows of an (n, 8) or (n, 16) array)."""
     rows = np.asarray(rows)
     limbs = rows.shape[-1] if rows.ndim > 1 else rows.size
     lo = hi = 0
@@ -67,7 +67,7 @@ def gather_partials(local, group=None) -> np.ndarray:
     return sum_partials(np.stack([b.cpu().numpy().view(np.uint64) for b in bufs]))
 
 
-def tor_sharded(ctx, O, chunk_bits: int, prec: str = "fp64", group=None):
+def tor_sharded(ctx, O, chunk_bits: int, prec: str, group=None):
     """This rank's chunk range on its GPU, gathered exactly; returns (TorResult, total limbs)."""
     import torch.distributed as dist
     from . import tor

@@ -24,8 +24,9 @@ _PREC = {"auto": PREC_AUTO, "fp64": PREC_FP64, "dd": PREC_DD, "fx128": PREC_FX12
 
 
 def partial_limbs(prec: str) -> int:
-    """64-bit limbs of one chunk partial: two 256-bit sums, or two 384-bit sums for fx256."""
-    return 12 if prec == "fx256" else 8
+    """64-bit limbs of one chunk partial: two 256-bit sums (128 fraction bits), or two 512-bit
+    sums (256 fraction bits) for fx256."""
+    return 16 if prec == "fx256" else 8
 _LAYOUT = {"xxpp": LAYOUT_XXPP, "xpxp": LAYOUT_XPXP}
 
 
@@ -91,7 +92,7 @@ SIGNATURES = {
     "tor_single_async": (_I, [_VP, _VP, _I, _I, _I, _I, _VP, _VP]),
     "tor_chunks": (_I, [_VP, _VP, _I, _I, _I, _I, _I, _U64, _U64, _VP, _VP]),
     "tor_fixed_to_result": (_I, [ctypes.POINTER(_U64), _I, _I, ctypes.POINTER(TorResultC)]),
-    "tor_fx256_mul": (_I, [_VP, _VP, _I, _VP, _VP, _VP]),
+    "tor_fx256_fma2": (_I, [_VP, _VP, _VP, _VP, _VP, _I, _VP, _VP, _VP]),
     "tor_levels_workspace": (_I, [_I, _I, ctypes.POINTER(ctypes.c_size_t)]),
     "tor_levels": (_I, [_VP, _I, _I, _I, _I, ctypes.POINTER(_I), _VP, ctypes.c_size_t, _VP, _VP]),
     "tor_levels_last_error": (ctypes.c_char_p, []),
@@ -103,6 +104,7 @@ SIGNATURES = {
     "tor_batch_reserve": (_I, [_VP, _I, _I]),
     "tor_batch_patterns": (_I, [_VP, _VP, _I, _I, _VP, _I, _I, _D, _VP, _VP]),
     "tor_fp64_peak": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "tor_int_peak": (_I, [_VP, ctypes.POINTER(_D)]),
     "tor_single_noalloc": (_I, [_VP, _I, _I, _I, _I, _VP, _VP]),
     "tor_mlp_create": (_I, [_VP, _I, _I, _U64, ctypes.POINTER(_VP)]),
     "tor_mlp_destroy": (None, [_VP]),
@@ -217,7 +219,7 @@ class Context:
     def set_chunk_bits(self, d: int):
         _check(self.lib.tor_set_chunk_bits(self.h, d))
 
-    def single(self, O: torch.Tensor, prec: str = "fp64", layout: str = "xxpp", tol: float = 1e-10,
+    def single(self, O: torch.Tensor, prec: str = "auto", layout: str = "xxpp", tol: float = 1e-10,
                stream=None) -> TorResult:
         """Tor(O) of one 2k x 2k matrix (blocking)."""
         k, ld = _mat(O)
@@ -226,7 +228,7 @@ class Context:
                                    _stream(stream), ctypes.byref(out)))
         return TorResult.from_c(out)
 
-    def single_async(self, O: torch.Tensor, out: torch.Tensor, prec: str = "fp64",
+    def single_async(self, O: torch.Tensor, out: torch.Tensor, prec: str,
                      layout: str = "xxpp", stream=None):
         """Enqueue Tor(O); the raw tor_result lands in the uint8 CUDA tensor `out`."""
         k, ld = _mat(O)
@@ -235,10 +237,10 @@ class Context:
         _check(self.lib.tor_single_async(self.h, O.data_ptr(), k, ld, _LAYOUT[layout], _PREC[prec],
                                          _stream(stream), out.data_ptr()))
 
-    def chunks(self, O: torch.Tensor, chunk_bits: int, c_begin: int, c_end: int, prec: str = "fp64",
+    def chunks(self, O: torch.Tensor, chunk_bits: int, c_begin: int, c_end: int, prec: str,
                layout: str = "xxpp", stream=None) -> torch.Tensor:
         """Exact per-chunk partials, an int64 CUDA tensor (c_end - c_begin, 8) of raw limbs
-        ((c_end - c_begin, 12) for fx256)."""
+        ((c_end - c_begin, 16) for fx256)."""
         k, ld = _mat(O)
         part = torch.zeros((max(c_end - c_begin, 0), partial_limbs(prec)), dtype=torch.int64, device=O.device)
         _check(self.lib.tor_chunks(self.h, O.data_ptr(), k, ld, _LAYOUT[layout], _PREC[prec],
@@ -284,7 +286,7 @@ class Context:
         _check(self.lib.tor_batch_reserve(self.h, n_max, k_max))
 
     def batch_async(self, ptrs: torch.Tensor, ks: torch.Tensor, lds: torch.Tensor, out: torch.Tensor,
-                    prec: str = "fp64", tol: float = 1e-10, layout: str = "xxpp", stream=None):
+                    prec: str = "auto", tol: float = 1e-10, layout: str = "xxpp", stream=None):
         """tor_batch on device arrays: ptrs int64, ks/lds int32, out uint8 (n * RESULT_BYTES)."""
         n = ptrs.numel()
         if out.numel() < n * RESULT_BYTES:
@@ -292,7 +294,7 @@ class Context:
         _check(self.lib.tor_batch(self.h, ptrs.data_ptr(), ks.data_ptr(), lds.data_ptr(), n, _LAYOUT[layout],
                                   _PREC[prec], tol, _stream(stream), out.data_ptr()))
 
-    def batch(self, Os, prec: str = "fp64", tol: float = 1e-10, layout: str = "xxpp", stream=None):
+    def batch(self, Os, prec: str = "auto", tol: float = 1e-10, layout: str = "xxpp", stream=None):
         """Tor of a list of 2k x 2k float64 CUDA tensors (blocking); returns a list of TorResult."""
         n = len(Os)
         if n == 0:
@@ -307,7 +309,7 @@ class Context:
         return [TorResult.from_bytes(raw[i * RESULT_BYTES:(i + 1) * RESULT_BYTES]) for i in range(n)]
 
     def batch_patterns_async(self, Ofull: torch.Tensor, patterns: torch.Tensor, out: torch.Tensor,
-                             prec: str = "fp64", tol: float = 1e-10, stream=None):
+                             prec: str = "auto", tol: float = 1e-10, stream=None):
         """tor_batch_patterns: patterns is an int64 CUDA tensor (n, ceil(M/64)) of bitsets."""
         k2, ld = _mat(Ofull)
         n = patterns.shape[0]
@@ -316,7 +318,7 @@ class Context:
         _check(self.lib.tor_batch_patterns(self.h, Ofull.data_ptr(), k2, ld, patterns.data_ptr(), n,
                                            _PREC[prec], tol, _stream(stream), out.data_ptr()))
 
-    def batch_patterns(self, Ofull: torch.Tensor, patterns, prec: str = "fp64", tol: float = 1e-10):
+    def batch_patterns(self, Ofull: torch.Tensor, patterns, prec: str = "auto", tol: float = 1e-10):
         """Tor(O_S) for each 0/1 pattern (rows of a (n, M) array-like); blocking."""
         M = Ofull.shape[0] // 2
         bits = pack_patterns(patterns, M).to(Ofull.device)
@@ -327,7 +329,7 @@ class Context:
 
     def sample_step(self, Ofull: torch.Tensor, logdet_sigma: float, patterns: torch.Tensor, logp: torch.Tensor,
                     logq: torch.Tensor, accepted: torch.Tensor, seed: int, step: int, marg_p=None,
-                    proposal=None, prec: str = "fp64", tol: float = 1e-10, k_cap: int = 0, stream=None):
+                    proposal=None, prec: str = "auto", tol: float = 1e-10, k_cap: int = 0, stream=None):
         """gbs_sample_step on device state tensors (patterns int64 (C, W), logp/logq float64, accepted int32)."""
         k2, ld = _mat(Ofull)
         C = patterns.shape[0]
@@ -338,7 +340,7 @@ class Context:
                                         seed & 0xFFFFFFFFFFFFFFFF, step & 0xFFFFFFFFFFFFFFFF, _PREC[prec], tol,
                                         int(k_cap), _stream(stream)))
 
-    def autotune(self, k: int, prec: str = "fp64", cache_path: str | None = None):
+    def autotune(self, k: int, prec: str, cache_path: str | None = None):
         """Time chunk depths and launch shapes for k clicks; returns (chunk_bits, blocks_per_sm)."""
         d, b = ctypes.c_int(), ctypes.c_int()
         _check(self.lib.tor_autotune(self.h, k, _PREC[prec], cache_path.encode() if cache_path else None,
@@ -364,8 +366,14 @@ class Context:
         _check(self.lib.tor_fp64_peak(self.h, ctypes.byref(r), ctypes.byref(c)))
         return r.value, c.value
 
+    def int_peak(self) -> float:
+        """Measured signed 32 x 32 -> 64-bit integer multiply-adds per second."""
+        r = ctypes.c_double()
+        _check(self.lib.tor_int_peak(self.h, ctypes.byref(r)))
+        return r.value
 
-def single_noalloc(O: torch.Tensor, out: torch.Tensor, prec: str = "fp64", layout: str = "xxpp",
+
+def single_noalloc(O: torch.Tensor, out: torch.Tensor, prec: str, layout: str = "xxpp",
                    stream=None):
     """tor_single_noalloc: enqueue Tor(O) with no device allocation; result bytes into `out`.
 
@@ -381,7 +389,7 @@ def single_noalloc(O: torch.Tensor, out: torch.Tensor, prec: str = "fp64", layou
 
 def fixed_to_result(limbs, k: int, tier: str = "fp64") -> TorResult:
     """Convert raw limbs (signed sum, sum_abs): 8 limbs of 256-bit fixed point with 128 fraction
-    bits, or 12 limbs of 384-bit fixed point with 192 fraction bits for fx256."""
+    bits, or 16 limbs of 512-bit fixed point with 256 fraction bits for fx256."""
     n = partial_limbs(tier)
     limbs = list(limbs)
     if len(limbs) != n:
@@ -427,20 +435,24 @@ def level_kth_mask(k: int, m: int, r: int) -> int:
     return out.value
 
 
-def fx256_mul(a: torch.Tensor, b: torch.Tensor):
-    """Elementwise 256-bit fixed-point products as the fx256 tier forms them: a, b int64 CUDA
-    tensors (n, 4) of little-endian limbs (value / 2^192); returns (products (n, 4), overflow (n,))."""
-    n = a.shape[0]
-    out = torch.zeros_like(a)
-    ovf = torch.zeros(n, dtype=torch.int32, device=a.device)
-    _check(load_library().tor_fx256_mul(a.data_ptr(), b.data_ptr(), n, out.data_ptr(), ovf.data_ptr(), None))
-    torch.cuda.synchronize(a.device)
+def fx256_fma2(s: torch.Tensor, a1: torch.Tensor, b1: torch.Tensor, a2: torch.Tensor, b2: torch.Tensor):
+    """Elementwise s + a1 b1 + a2 b2 as the fx256 tier's Schur updates form it: int32 CUDA tensors
+    (n, 9) of limbs (value = sum_i l_i 2^(29 i - 203)); returns (result (n, 9), overflow (n,))."""
+    n = s.shape[0]
+    for x in (s, a1, b1, a2, b2):
+        if x.dtype != torch.int32 or tuple(x.shape) != (n, 9) or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("operands must be contiguous int32 CUDA tensors of shape (n, 9)")
+    out = torch.zeros_like(s)
+    ovf = torch.zeros(n, dtype=torch.int32, device=s.device)
+    _check(load_library().tor_fx256_fma2(s.data_ptr(), a1.data_ptr(), b1.data_ptr(), a2.data_ptr(),
+                                         b2.data_ptr(), n, out.data_ptr(), ovf.data_ptr(), None))
+    torch.cuda.synchronize(s.device)
     return out, ovf
 
 
 def limbs_to_int(limbs) -> int:
     """Signed Python integer of L little-endian 64-bit limbs (value = int / 2^(32 L): 4 limbs
-    with 128 fraction bits, or 6 limbs with 192 for fx256)."""
+    with 128 fraction bits, or 8 limbs with 256 for fx256)."""
     limbs = list(limbs)
     v = 0
     for i, x in enumerate(limbs):
@@ -540,6 +552,6 @@ def default_context(device: int = 0) -> Context:
     return _default
 
 
-def tor_single(O: torch.Tensor, prec: str = "fp64", layout: str = "xxpp", tol: float = 1e-10,
+def tor_single(O: torch.Tensor, prec: str = "auto", layout: str = "xxpp", tol: float = 1e-10,
                stream=None) -> TorResult:
     return default_context(O.device.index or 0).single(O, prec=prec, layout=layout, tol=tol, stream=stream)

@@ -26,28 +26,36 @@ def test_hbm_peak_prefers_the_measured_file(tmp_path, monkeypatch):
     assert v == 7000.5 and "measured" in src
 
 
-def test_walk_traffic_only_while_the_sources_match(tmp_path, monkeypatch):
-    # a copy of the walk's sources with a profile line keyed by their hash
-    src_dir = tmp_path / "paper_2009_01177_gb300" / "csrc"
-    src_dir.mkdir(parents=True)
-    for f in bench.WALK_SOURCES:
+@pytest.mark.parametrize("kernel", sorted(bench.KERNEL_SOURCES))
+def test_recorded_traffic_only_while_the_sources_match(tmp_path, monkeypatch, kernel):
+    # a copy of the kernel's sources with a profile line keyed by their hash
+    (tmp_path / "paper_2009_01177_gb300" / "csrc").mkdir(parents=True)
+    for f in bench.KERNEL_SOURCES[kernel]:
         with open(os.path.join(bench.ROOT, f), "rb") as fh:
             (tmp_path / f).write_bytes(fh.read())
     (tmp_path / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    sha = bench.walk_sources_sha256()
-    (tmp_path / "profiles" / "k_dfs_fp64_k32.md").write_text(
-        f"traffic_bytes_per_launch = 1.25e11 (walk sources sha256 {sha})\n")
-    assert bench.walk_traffic(32) == 1.25e11
-    assert bench.walk_traffic(30) is None                          # no summary for that size
-    with open(tmp_path / bench.WALK_SOURCES[0], "ab") as fh:       # any edit to the kernel's sources
+    sha = bench.sources_sha256(kernel)
+    (tmp_path / "profiles" / f"{kernel}_k32.md").write_text(
+        f"traffic_bytes_per_launch = 1.25e11 (sources sha256 {sha})\n")
+    assert bench.recorded_traffic(kernel, 32) == 1.25e11
+    assert bench.recorded_traffic(kernel, 30) is None                  # no summary for that size
+    with open(tmp_path / bench.KERNEL_SOURCES[kernel][0], "ab") as fh:  # any edit to the kernel's sources
         fh.write(b"\n// changed\n")
-    assert bench.walk_traffic(32) is None
+    assert bench.recorded_traffic(kernel, 32) is None
 
 
-def test_committed_summary_matches_the_committed_sources():
-    # the figure in the repository is for the sources in the repository
-    assert bench.walk_traffic(32) is not None
+def test_walk_operation_model():
+    # the walk over r modes visits every non-empty subset once (one pivot each); per subset it
+    # approaches 1 pivot, 1/2 coefficient set, 2 pivot rows and 7 Schur entries (Sum 2^-n-1 n(2n+1))
+    for r in (1, 2, 5):
+        p, c, rows, e, n = bench.walk_ops(r)
+        assert n == 2 ** r and p == 2 ** r - 1
+    assert bench.walk_ops(2)[1:4] == (1, 2, 3)       # one child with one mode: one 3-entry update
+    p, c, rows, e, n = bench.walk_ops(32)
+    assert abs(p / n - 1) < 1e-9 and abs(c / n - 0.5) < 1e-9
+    assert abs(rows / n - 2) < 1e-6 and abs(e / n - 7) < 1e-6
+    assert bench.fx256_macs_per_subset(32) == pytest.approx(60 * 33, rel=1e-6)
 
 
 def test_dram_rate_of_the_walk(tmp_path, monkeypatch):

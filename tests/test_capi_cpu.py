@@ -72,35 +72,35 @@ def test_fixed_point_conversion_on_host(lib):
     assert (r.hi, r.lo) == (1.0, 2.0 ** -100)
 
 
-def test_fixed_point_conversion_of_384_bit_partials(lib):
-    # the 256-bit tier's partials: two 6-limb values with 192 fraction bits
+def test_fixed_point_conversion_of_512_bit_partials(lib):
+    # the 256-bit-class tier's partials: two 8-limb values with 256 fraction bits
     from paper_2009_01177_gb300 import tor
     tor.load_library()
 
-    def limbs6(v):
-        v &= (1 << 384) - 1
-        return [(v >> (64 * i)) & 0xFFFFFFFFFFFFFFFF for i in range(6)]
+    def limbs8(v):
+        v &= (1 << 512) - 1
+        return [(v >> (64 * i)) & 0xFFFFFFFFFFFFFFFF for i in range(8)]
 
-    r = tor.fixed_to_result(limbs6(3 << 192) + limbs6(5 << 192), 7, "fx256")
+    r = tor.fixed_to_result(limbs8(3 << 256) + limbs8(5 << 256), 7, "fx256")
     assert (r.hi, r.lo, r.sum_abs, r.tier) == (3.0, 0.0, 5.0, 4)
-    # -(2^-100 + 2^-190): its low part lies far below the 128-bit tiers' resolution
-    v = -((1 << 92) + (1 << 2))
-    r = tor.fixed_to_result(limbs6(v) + limbs6(1 << 192), 7, "fx256")
-    assert (r.hi, r.lo) == (-(2.0 ** -100), -(2.0 ** -190))
-    # error model: 4k u sum_abs with u = 2^-186
-    assert r.err_est == 4 * 7 * 2.0 ** -186 * 1.0
+    # -(2^-100 + 2^-200): its low part lies far below the 128-bit tiers' resolution
+    v = -((1 << 156) + (1 << 56))
+    r = tor.fixed_to_result(limbs8(v) + limbs8(1 << 256), 7, "fx256")
+    assert (r.hi, r.lo) == (-(2.0 ** -100), -(2.0 ** -200))
+    # error model: 4k u sum_abs with u = 2^-196
+    assert r.err_est == 4 * 7 * 2.0 ** -196 * 1.0
     with pytest.raises(ValueError):
-        tor.fixed_to_result(limbs6(1) + limbs6(1), 7, "fp64")   # 12 limbs given, 8 expected
+        tor.fixed_to_result(limbs8(1) + limbs8(1), 7, "fp64")   # 16 limbs given, 8 expected
 
 
-def test_shard_sums_of_384_bit_partials():
+def test_shard_sums_of_512_bit_partials():
     from paper_2009_01177_gb300 import shard
-    a = shard.ints_to_limbs(-(1 << 300), 1 << 300, limbs=12)
-    b = shard.ints_to_limbs(3, 7, limbs=12)
+    a = shard.ints_to_limbs(-(1 << 400), 1 << 400, limbs=16)
+    b = shard.ints_to_limbs(3, 7, limbs=16)
     tot = shard.sum_partials(np.stack([a, b]))
-    assert tot.shape == (12,)
+    assert tot.shape == (16,)
     lo, hi = shard.limbs_to_ints(tot)
-    assert lo == (3 - (1 << 300)) % (1 << 384) and hi == (1 << 300) + 7
+    assert lo == (3 - (1 << 400)) % (1 << 512) and hi == (1 << 400) + 7
 
 
 def test_bad_arguments_are_refused_before_any_device_call(lib):
@@ -165,5 +165,5 @@ def test_bad_arguments_are_refused_before_any_device_call(lib):
     assert L.tor_level_kth_mask(3, 1, 3, ctypes.byref(mask)) == EINVAL   # C(3, 1) = 3 ranks
 
     # the 256-bit product helper
-    assert L.tor_fx256_mul(None, None, -1, None, None, None) == EINVAL
-    assert L.tor_fx256_mul(None, dummy, 1, dummy, dummy, None) == EINVAL
+    assert L.tor_fx256_fma2(None, None, None, None, None, -1, None, None, None) == EINVAL
+    assert L.tor_fx256_fma2(None, dummy, dummy, dummy, dummy, 1, dummy, dummy, None) == EINVAL

@@ -50,8 +50,8 @@ def test_batch_matches_single_and_oracle(ctx, prec):
 
 def test_batch_is_deterministic(ctx):
     dmats = [torch.from_numpy(O).cuda() for O in mats_uneven(seed=9, n=64, k_hi=20)]
-    a = ctx.batch(dmats)
-    b = ctx.batch(dmats)
+    a = ctx.batch(dmats, prec="fp64")
+    b = ctx.batch(dmats, prec="fp64")
     assert [(x.hi, x.lo, x.sum_abs) for x in a] == [(x.hi, x.lo, x.sum_abs) for x in b]
 
 
@@ -59,7 +59,7 @@ def test_batch_statuses(ctx, cuda_lib):
     good = gi.workload_m16_k10()[2]
     bad = 2.0 * np.eye(8)
     dm = [torch.from_numpy(O).cuda() for O in (good, bad, np.zeros((0, 0)), good)]
-    res = ctx.batch(dm)
+    res = ctx.batch(dm, prec="fp64")
     assert res[0].status == 0 and res[3].status == 0
     assert (res[0].hi, res[0].lo) == (res[3].hi, res[3].lo)
     assert res[1].status == cuda_lib.TOR_ENOTPD
@@ -74,7 +74,7 @@ def test_batch_rejects_k_beyond_reservation(ctx, cuda_lib):
     ks = torch.tensor([4, 9], dtype=torch.int32, device="cuda")
     lds = torch.tensor([8, 18], dtype=torch.int32, device="cuda")
     out = torch.zeros(2 * cuda_lib.RESULT_BYTES, dtype=torch.uint8, device="cuda")
-    ctx.batch_async(ptrs, ks, lds, out)
+    ctx.batch_async(ptrs, ks, lds, out, prec="fp64")
     r = cuda_lib.results_from_tensor(out, 2)
     assert r[0].status == 0 and abs(r[0].value - (0.25) ** 4) < 1e-14
     assert r[1].status == cuda_lib.TOR_EINVAL
@@ -87,7 +87,7 @@ def test_batch_auto_mixes_tiers(ctx, cuda_lib):
     tol = 1e-8
     res = ctx.batch(dm, prec="auto", tol=tol)
     tiers = {r.tier for r in res}
-    assert 1 in tiers and len(tiers) >= 2 and tiers <= {1, 2, 3}
+    assert 1 in tiers and len(tiers) >= 2 and tiers <= {1, 2, 3, 4}
     for O, r in zip(mats, res):
         ref = oracle.tor(O)
         if r.status == cuda_lib.TOR_EPREC:
@@ -105,6 +105,44 @@ def test_batch_fixed_point_tier(ctx, cuda_lib):
         assert r.status == 0 and r.tier == 3
         assert err(r, ref) <= r.err_est
     assert res[-1].status == cuda_lib.TOR_EINVAL      # outside the fixed-point range: refused
+
+
+def test_batch_fx256_tier_against_the_exact_oracle(ctx, cuda_lib):
+    # explicit 256-bit batches, per-instance matrices and click patterns of one state; the
+    # last instance (t_max = 10^40 > 2^26) lies outside the range and is refused
+    st, pat, O32 = gi.workload_m100(32)
+    ks = (0, 1, 3, 7, 11, 14)
+    mats = [gi.select(st.O, pat[:k]) for k in ks] + [0.99 * np.eye(40)]
+    res = ctx.batch([torch.from_numpy(O).cuda() for O in mats], prec="fx256")
+    P = np.zeros((len(ks), 100), dtype=np.uint8)
+    for row, k in enumerate(ks):
+        P[row, pat[:k]] = 1
+    res_p = ctx.batch_patterns(torch.from_numpy(st.O).cuda(), P, prec="fx256")
+    for k, O, r, rp in zip(ks, mats, res, res_p):
+        ref_t, ref_s = oracle.tor_exact(O)
+        for x in (r, rp):
+            assert x.status == 0 and x.tier == 4, (k, x)
+            assert abs(Fraction(x.hi) + Fraction(x.lo) - ref_t) <= Fraction(x.err_est) + abs(ref_t) * Fraction(1, 2 ** 104)
+            assert abs(x.sum_abs - float(ref_s)) <= 1e-15 * float(ref_s)
+        assert (r.hi, r.lo) == (rp.hi, rp.lo)          # the same chunks, the same exact sums
+    assert res[-1].status == cuda_lib.TOR_EINVAL
+
+
+def test_batch_auto_reaches_256_bits(ctx, cuda_lib):
+    # kappa grows with k: at tol = 1e-25 the FP64 and 128-bit tiers fall short and the
+    # escalation has to end in the 256-bit tier; every result meets tol against the exact sum
+    st, pat, O32 = gi.workload_m100(32)
+    ks = (4, 10, 16, 20)
+    mats = [gi.select(st.O, pat[:k]) for k in ks]
+    tol = 1e-25
+    res = ctx.batch([torch.from_numpy(O).cuda() for O in mats], prec="auto", tol=tol)
+    assert 4 in {r.tier for r in res}
+    for k, O, r in zip(ks, mats, res):
+        ref_t, ref_s = oracle.tor_exact(O)
+        assert r.status == 0, (k, r)
+        e = abs(Fraction(r.hi) + Fraction(r.lo) - ref_t)
+        assert e <= Fraction(r.err_est) + abs(ref_t) * Fraction(1, 2 ** 104)
+        assert r.err_est <= tol * abs(float(ref_t))
 
 
 def test_batch_auto_escalates_through_fixed_point(ctx, cuda_lib):
@@ -144,18 +182,18 @@ def test_batch_in_cuda_graph_replays_with_new_inputs(ctx, cuda_lib):
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
-        ctx.batch_async(ptrs, ks, lds, out, stream=s)      # warm-up outside capture
+        ctx.batch_async(ptrs, ks, lds, out, prec="fp64", stream=s)      # warm-up outside capture
     torch.cuda.current_stream().wait_stream(s)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
-        ctx.batch_async(ptrs, ks, lds, out, stream=s)
+        ctx.batch_async(ptrs, ks, lds, out, prec="fp64", stream=s)
     for mats in (A, Bm):
         load(mats)
         g.replay()
         torch.cuda.synchronize()
         res = cuda_lib.results_from_tensor(out, n)
-        direct = ctx.batch([torch.from_numpy(O).cuda() for O in mats])
+        direct = ctx.batch([torch.from_numpy(O).cuda() for O in mats], prec="fp64")
         assert [(r.hi, r.lo) for r in res] == [(r.hi, r.lo) for r in direct]
 
 
@@ -166,10 +204,10 @@ def test_batches_accept_larger_k_after_small(cuda_lib):
         st, pat, O32 = gi.workload_m100(32)
         small = [torch.from_numpy(gi.select(st.O, pat[:6])).cuda() for _ in range(3)]
         big = [torch.from_numpy(gi.select(st.O, pat[:k])).cuda() for k in (14, 17, 9)]
-        assert all(r.status == 0 for r in c.batch(small))
-        res = c.batch(big)
+        assert all(r.status == 0 for r in c.batch(small, prec="fp64"))
+        res = c.batch(big, prec="fp64")
         for Od, r in zip(big, res):
-            ref = c.single(Od)
+            ref = c.single(Od, prec="fp64")
             assert r.status == 0
             assert abs(r.value - ref.value) <= r.err_est + ref.err_est
     finally:
@@ -184,10 +222,10 @@ def test_pattern_batches_accept_larger_k_after_small(ctx):
     small[:, :3] = 1
     big = np.zeros((4, 30), dtype=np.uint8)
     big[:, :18] = 1
-    ctx.batch_patterns(Od, small)
-    res = ctx.batch_patterns(Od, big)
+    ctx.batch_patterns(Od, small, prec="fp64")
+    res = ctx.batch_patterns(Od, big, prec="fp64")
     assert all(r.status == 0 for r in res)
-    ref = ctx.single(torch.from_numpy(gi.select(st.O, np.arange(18))).cuda())
+    ref = ctx.single(torch.from_numpy(gi.select(st.O, np.arange(18))).cuda(), prec="fp64")
     assert abs(res[0].value - ref.value) <= res[0].err_est + ref.err_est
 
 
