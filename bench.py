@@ -473,51 +473,66 @@ def run_levels(args):
 
 
 def run_batch(args):
-    """Batched Tor/s for 4096 patterns (k in [8, 30]) against one launch per pattern."""
+    """Batched Tor/s for 4096 patterns (k in [8, 30]) at tol, against the same Torontonians
+    one launch each at the tier the batch settled on (equal accuracy)."""
     import torch
     from paper_2009_01177_gb300 import gbs_inputs as gi
     from paper_2009_01177_gb300 import tor
+    tol = args.tol
     st, pats = batch_patterns_m100(args.n)
     ks = pats.sum(1)
     subsets = float((2.0 ** ks).sum())
     ctx = tor.Context(0)
     Od = torch.from_numpy(st.O).cuda()
     P = tor.pack_patterns(pats, st.M).cuda()
-    out = torch.zeros(len(pats) * tor.RESULT_BYTES, dtype=torch.uint8, device="cuda")
-    for _ in range(args.warmup):
-        ctx.batch_patterns_async(Od, P, out)
+    n = len(pats)
+    out = torch.zeros(n * tor.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    warm = tor.pack_patterns(pats[:64], st.M).cuda()
+    for _ in range(args.warmup):              # warm-up on a 64-pattern slice of the same batch
+        ctx.batch_patterns_async(Od, warm, out, prec="auto", tol=tol)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clocks:
         e0.record()
         for _ in range(args.steps):
-            ctx.batch_patterns_async(Od, P, out)
+            ctx.batch_patterns_async(Od, P, out, prec="auto", tol=tol)
         e1.record()
         torch.cuda.synchronize()
     tb = e0.elapsed_time(e1) / 1e3 / args.steps
-    res = tor.results_from_tensor(out, len(pats))
-    # the same Torontonians, one tor_single_async launch each (matrices formed beforehand)
+    res = tor.results_from_tensor(out, n)
+    tiers = [TIER_NAME.get(r.tier, "none") for r in res]
+    ok = [r.status == 0 and r.err_est <= tol * abs(r.value) for r in res]
+    ratio = [r.err_est / abs(r.value) if r.value else float("inf") for r in res]
+    # the same Torontonians, one tor_single_async launch each at the batch's final tier
     mats = [torch.from_numpy(gi.select(st.O, np.nonzero(x)[0])).cuda() for x in pats]
-    o1 = torch.zeros(tor.RESULT_BYTES, dtype=torch.uint8, device="cuda")
-    ctx.single_async(mats[0], o1)
+    o1 = torch.zeros(n * tor.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    ctx.single_async(mats[0], o1[:tor.RESULT_BYTES], prec=tiers[0] if tiers[0] != "none" else "fp64")
     torch.cuda.synchronize()
     e0.record()
-    for m in mats:
-        ctx.single_async(m, o1)
+    for i, m in enumerate(mats):
+        if tiers[i] != "none":
+            ctx.single_async(m, o1[i * tor.RESULT_BYTES:(i + 1) * tor.RESULT_BYTES], prec=tiers[i])
     e1.record()
     torch.cuda.synchronize()
     ts = e0.elapsed_time(e1) / 1e3
-    line = {"metric": "batched Tor/s (4096 patterns, k in [8,30])", "value": len(pats) / tb, "unit": "Tor/s",
+    res1 = tor.results_from_tensor(o1, n)
+    agree = sum(abs(a.value - b.value) <= a.err_est + b.err_est for a, b, t in zip(res, res1, tiers) if t != "none")
+    line = {"metric": "batched Tor/s (4096 patterns, k in [8,30]) at tol", "value": n / tb, "unit": "Tor/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tb,
-            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{len(pats)} click patterns of a synthetic M=100 lossy GBS state "
+            "higher_is_better": True, "dtype": "auto: " + ", ".join(sorted(set(tiers))), "data": "synthetic",
+            "config": {"workload": f"{n} click patterns of a synthetic M=100 lossy GBS state "
                                    "(r~U[0.6,1.2], eta=0.3, seed 4): independent clicks with the exact "
                                    "single-mode marginals, kept if 8 <= k <= 30", "k_mean": float(ks.mean()),
-                       "subsets": subsets, "tier": "fp64"},
+                       "subsets": subsets, "prec": "auto", "tol": tol,
+                       "warmup": "on a 64-pattern slice of the batch"},
             "subset_dets_per_s": subsets / tb,
-            "one_launch_each": {"Tor/s": len(pats) / ts, "subset_dets_per_s": subsets / ts, "s": ts},
+            "tiers": {t: tiers.count(t) for t in sorted(set(tiers))},
+            "resolved": int(sum(ok)), "eprec": int(sum(r.status == tor.TOR_EPREC for r in res)),
+            "max_err_est_over_tor": float(max(ratio)),
+            "one_launch_each": {"Tor/s": n / ts, "subset_dets_per_s": subsets / ts, "s": ts,
+                                "tiers": "each instance at the batch's final tier",
+                                "agree_within_bounds": int(agree)},
             "speedup_vs_one_launch_each": ts / tb,
-            "statuses_ok": int(sum(r.status == 0 for r in res)),
             "clocks": clocks.summary()}
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -565,17 +580,28 @@ def run_mh(args):
                     pat=torch.zeros((C, words), dtype=torch.int64, device="cuda"),
                     logp=torch.full((C,), -math.inf, dtype=torch.float64, device="cuda"),
                     logq=torch.zeros(C, dtype=torch.float64, device="cuda"),
-                    acc=torch.zeros(C, dtype=torch.int32, device="cuda"),
+                    acc=torch.zeros(C, dtype=torch.int32, device="cuda"), C=C,
                     marg=torch.tensor(marginals(st), dtype=torch.float64, device="cuda"))
 
-    def run(ch, steps, seed, prop=None, record=None, t0=0, k_cap=0):
+    tol = args.mh_tol
+    causes = {}   # rejections that were not the Metropolis test, by cause, per run label
+
+    def run(ch, steps, seed, prop=None, record=None, t0=0, k_cap=0, label=None):
+        """steps MH steps; the mean acceptance.  Every Torontonian comes from the AUTO path at
+        tol; rejections for other reasons than the Metropolis test are counted by cause."""
         acc = torch.zeros((), dtype=torch.float64, device="cuda")
+        cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
         for s_ in range(steps):
             ctx.sample_step(ch["O"], ch["logdet"], ch["pat"], ch["logp"], ch["logq"], ch["acc"], seed, t0 + s_,
-                            marg_p=ch["marg"], proposal=prop, prec="fp64", k_cap=k_cap)
-            acc += ch["acc"].double().mean()
+                            marg_p=ch["marg"], proposal=prop, prec="auto", tol=tol, k_cap=k_cap)
+            a = ch["acc"]
+            acc += (a == 1).double().mean()
+            cnt += torch.stack([(a == -1).sum(), (a == -2).sum(), (a == -3).sum()])
             if record is not None:
                 record.append(ch["pat"].clone())
+        if label is not None:
+            c = cnt.tolist()
+            causes[label] = {"over_k_cap": c[0], "missed_tol": c[1], "failed": c[2], "proposals": steps * ch["C"]}
         return float(acc) / steps
 
     def train(net, pats, w, iters, batch, lr, val=None, val_w=None, resample=False):
@@ -615,7 +641,7 @@ def run_mh(args):
     ch = chains(st)
     hist = []
     progress(f"M=60 plain exact chain, k_cap={k_cap}")
-    run(ch, 60, 6, record=hist, k_cap=k_cap)
+    run(ch, 60, 6, record=hist, k_cap=k_cap, label="training_chain")
     progress("training the proposal")
     pool = torch.cat(hist[10:])
     pool = pool[torch.randperm(pool.shape[0], device="cuda")]
@@ -635,12 +661,12 @@ def run_mh(args):
     Pis = tor.pack_patterns(X, st.M).cuda()
     ois = torch.zeros(X.shape[0] * tor.RESULT_BYTES, dtype=torch.uint8, device="cuda")
     t_is = time.perf_counter()
-    ctx.batch_patterns_async(O60, Pis, ois, prec="fp64")
+    ctx.batch_patterns_async(O60, Pis, ois, prec="auto", tol=tol)
     torch.cuda.synchronize()
     t_is = time.perf_counter() - t_is
     ris = tor.results_array(ois, X.shape[0])
     tor_v = ris["hi"] + ris["lo"]
-    ok = (ris["status"] == 0) & (tor_v > 0)
+    ok = (ris["status"] == 0) & (tor_v > 0) & (ris["err_est"] <= tol * np.abs(tor_v))
     logdet60 = float(np.linalg.slogdet(st.Sigma)[1])
     logp_is = np.log(np.where(ok, tor_v, 1.0)) - 0.5 * logdet60
     logq_is = (X * np.log(marg60) + (1 - X) * np.log1p(-marg60)).sum(1)
@@ -666,7 +692,7 @@ def run_mh(args):
         series = []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        acc = run(chn, steps, 7, prop, record=series, t0=100, k_cap=k_cap)
+        acc = run(chn, steps, 7, prop, record=series, t0=100, k_cap=k_cap, label=name)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         ess = _ess_geyer(np.stack([_click_counts(p) for p in series]).astype(float))
@@ -674,7 +700,8 @@ def run_mh(args):
                      "ess_per_s": ess * C / el, "ess_per_chain": ess, "s": el, "steps": steps}
     out = {"metric": "accepted samples/s, learned vs plain proposal (M=60)", "unit": "samples/s",
            "value": res["learned"]["accepted_samples_per_s"], "n_gpus": 1, "higher_is_better": True,
-           "dtype": "f64 Torontonians, bf16 network", "data": "synthetic", "plain": res["plain"],
+           "dtype": "Torontonians by the AUTO path at tol (tiers as the bound pass routes), bf16 network",
+           "data": "synthetic", "tol": tol, "rejections_not_by_the_test": causes, "plain": res["plain"],
            "learned": res["learned"],
            "speedup_accepted": res["learned"]["accepted_samples_per_s"] / res["plain"]["accepted_samples_per_s"],
            "speedup_ess": res["learned"]["ess_per_s"] / max(res["plain"]["ess_per_s"], 1e-30),
@@ -723,7 +750,7 @@ def run_mh(args):
         for cp in checkpoints:              # time only the steps; TV of all states pooled so far
             torch.cuda.synchronize()
             t0s = time.perf_counter()
-            run(chn, cp - done, 9, prop, record=series, t0=20 + done)
+            run(chn, cp - done, 9, prop, record=series, t0=20 + done, label=f"m20_{name}")
             torch.cuda.synchronize()
             el += time.perf_counter() - t0s
             done = cp
@@ -966,6 +993,7 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-10, help="relative tolerance every result must meet")
     ap.add_argument("--no-fp64", action="store_true", help="single mode: skip the secondary FP64 walk timing")
     ap.add_argument("--n", type=int, default=4096, help="patterns (batch) or chains (mh)")
+    ap.add_argument("--mh-tol", type=float, default=1e-8, help="mh mode: tolerance of every exact Torontonian")
     ap.add_argument("--chunk-bits", type=int, default=None,
                     help="single mode: chunk depth d instead of the autotuner's choice")
     ap.add_argument("--blocks-per-sm", type=int, default=4, help="with --chunk-bits: resident blocks per SM")

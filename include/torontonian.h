@@ -270,25 +270,31 @@ int tor_level_kth_mask(int k, int m, uint64_t r, uint64_t *mask);
 int tor_fx256_fma2(const int32_t *s_dev, const int32_t *a1_dev, const int32_t *b1_dev, const int32_t *a2_dev,
                    const int32_t *b2_dev, int n, int32_t *out_dev, int *ovf_dev, cudaStream_t stream);
 
-/* Convert one fixed-point pair as written by tor_chunks (8 limbs, or 12 for
+/* Convert one fixed-point pair as written by tor_chunks (8 limbs, or 16 for
  * TOR_PREC_FX256), possibly summed over shards, to a tor_result (host, no
  * GPU needed). */
 int tor_fixed_to_result(const uint64_t *limbs, int k, int tier, tor_result *out);
 
 /*
  * tor_batch: Tor of n matrices of different k (e.g. the patterns a sampler
- * proposes), scheduled on the device: a plan kernel lays all (instance,
- * chunk) pairs on one item axis per tier, sorted by chunk size, and one
- * persistent walk kernel per tier drains it; partial sums are added exactly
- * per instance.  Asynchronous; no host round trip once the workspace is
- * reserved, so the whole call can be captured in a CUDA graph.
+ * proposes), each by Eq. 2 (Sec. 3.1): the alternating sum over all 2^k_i
+ * subsets Z of 1/sqrt(det(I - O_Z)), with Algorithm 1's balanced partition of
+ * each instance's subsets into equal prefix chunks.  Scheduled on the
+ * device: a plan kernel lays all (instance, chunk) pairs on one item axis per
+ * tier, sorted by chunk size, and one persistent walk kernel per tier drains
+ * it; partial sums are added exactly per instance.  Asynchronous; no host
+ * round trip once the workspace is reserved, so the whole call can be
+ * captured in a CUDA graph.
  *   O     dev  array of n device pointers (each 2k_i x 2k_i FP64, `layout`).
  *   k,ld  dev  arrays of n ints.
- *   prec  TOR_PREC_FP64, TOR_PREC_DD, TOR_PREC_FX128 (instances outside the
- *         fixed-point range get TOR_EINVAL), or TOR_PREC_AUTO (per-instance
- *         tier from the bound pass; results whose err_est exceeds
- *         tol * |Tor| are recomputed one tier up as in tor_single, in up to
- *         two more rounds; results still above get status TOR_EPREC).
+ *   prec  TOR_PREC_FP64, TOR_PREC_DD, TOR_PREC_FX128 or TOR_PREC_FX256
+ *         (instances outside a fixed-point tier's range get TOR_EINVAL), or
+ *         TOR_PREC_AUTO (per-instance tier from the bound pass, the
+ *         precision choice of Sec. 5.4; results whose err_est exceeds
+ *         tol * |Tor| are recomputed in the next tier with more precision that
+ *         holds them, FP64 -> FX128 -> FX256, double-double outside the
+ *         fixed-point ranges, in up to two more rounds; results still above
+ *         get status TOR_EPREC).
  *   out   dev  n results; per-instance status TOR_OK, TOR_ENOTPD, TOR_EPREC,
  *         or TOR_EINVAL (k outside [0, TOR_MAX_K], or above the k_max of an
  *         explicit tor_batch_reserve).
@@ -396,7 +402,13 @@ int tor_mlp_sample(tor_mlp *m, int B, uint64_t seed, uint64_t step, uint64_t *pa
  *                 logp = -inf marks an uninitialised chain (accepts any
  *                 proposal with p > 0).  After retraining the network, refresh
  *                 logq of the current states with tor_mlp_logq.
- *   accepted      dev  C ints, 1 where the proposal was accepted.
+ *   accepted      dev  C ints: 1 the proposal was accepted; 0 it was rejected
+ *                 by the Metropolis-Hastings test; negative, it was rejected
+ *                 because p(S') is not known to the tolerance, so that callers
+ *                 can count those rejections: -1 more clicks than k_cap (not
+ *                 evaluated), -2 its Torontonian missed tol in the most precise
+ *                 tier whose range holds it (TOR_EPREC), -3 any other failed
+ *                 evaluation (not positive definite, out of range) or Tor <= 0.
  *   seed, step    Philox4x32-10 key and counter: draw j of chain c is at
  *                 (seed; step, c, j), j < M for the proposal, j = M to accept.
  *   prec, tol     tier for the exact Torontonians, as for tor_batch.

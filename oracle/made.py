@@ -105,21 +105,34 @@ def magnitude_logits(theta, X, M, H):
     return a3 @ np.abs(W4).T + np.abs(b4)
 
 
-def grad_magnitude(theta, X, w, M, H):
+def grad_magnitude(theta, X, w, M, H, dl_extra=None):
     """The backward pass run on magnitudes (|dL/dl|, |W|, |x|, ReLU gates of the
     real pass): the scale of each gradient entry's sum of products, used to
-    bound low-precision rounding of the gradient."""
+    bound low-precision rounding of the gradient.  dl_extra (B x M), if given,
+    is added to |dL/dl| (an error already present in dL/dl, carried through)."""
     W1, b1, W2, b2, W3, b3, W4, b4 = unflatten(theta, M, H)
     w = np.asarray(w, dtype=np.float64)
     wn = w / w.sum()
     l, (X, h1, h2, h3) = forward(theta, X, M, H)
     dl = np.abs(wn[:, None] * (1.0 / (1.0 + np.exp(-l)) - X))
+    if dl_extra is not None:
+        dl = dl + dl_extra
     m3 = (dl @ np.abs(W4)) * (h3 > 0)
     m2 = (m3 @ np.abs(W3)) * (h2 > 0)
     m1 = (m2 @ np.abs(W2)) * (h1 > 0)
     parts = [m1.T @ np.abs(X), m1.sum(0), m2.T @ np.abs(h1), m2.sum(0), m3.T @ np.abs(h2), m3.sum(0),
              dl.T @ np.abs(h3), dl.sum(0)]
     return flatten(parts)
+
+
+def preactivations(theta, X, M, H):
+    """The three hidden layers' pre-activations (B x H each), float64."""
+    W1, b1, W2, b2, W3, b3, W4, b4 = unflatten(theta, M, H)
+    X = np.asarray(X, dtype=np.float64)
+    z1 = X @ W1.T + b1
+    z2 = np.maximum(z1, 0.0) @ W2.T + b2
+    z3 = np.maximum(z2, 0.0) @ W3.T + b3
+    return z1, z2, z3
 
 
 def all_patterns(M: int) -> np.ndarray:
@@ -136,3 +149,18 @@ def random_theta(M, H, seed, scale=1.0):
             p = p * mk[i // 2]
         parts.append(p)
     return flatten(parts)
+
+
+def adam_step(theta, grad, m, v, t, lr, mask=None, b1=0.9, b2=0.999, eps=1e-8):
+    """One masked Adam step (Kingma & Ba, ICLR 2015, Algorithm 1) in float64: t is the
+    1-based step number; masked entries (mask 0) are not parameters: their gradient counts
+    as zero and they stay at zero.  Returns (theta, m, v) after the step."""
+    theta = np.asarray(theta, dtype=np.float64)
+    mk = np.ones_like(theta) if mask is None else np.asarray(mask, dtype=np.float64)
+    g = np.asarray(grad, dtype=np.float64) * mk
+    m = b1 * np.asarray(m, dtype=np.float64) + (1.0 - b1) * g        # first moment
+    v = b2 * np.asarray(v, dtype=np.float64) + (1.0 - b2) * g * g    # second moment
+    m_hat = m / (1.0 - b1 ** t)                                       # bias corrections
+    v_hat = v / (1.0 - b2 ** t)
+    theta = (theta - lr * m_hat / (np.sqrt(v_hat) + eps)) * mk
+    return theta, m, v

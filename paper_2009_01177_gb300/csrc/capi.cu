@@ -723,7 +723,7 @@ int gbs_sample_step(tor_ctx *ctx, const double *O, int M, int ld, double logdet_
   }
   if ((rc = batch_patterns(ctx, O, M, ld, (const uint64_t *)prop, C, prec, tol, s, res, k_cap > 0 ? k_cap : -1)))
     return rc;
-  if (tor::launch_accept(C, M, words, logdet_sigma, res, prop, lq_prop, (unsigned long long *)patterns, logp, logq,
+  if (tor::launch_accept(C, M, words, k_cap, logdet_sigma, res, prop, lq_prop, (unsigned long long *)patterns, logp, logq,
                          accepted, seed, step, s))
     return fail(TOR_ECUDA, "accept: %s", cudaGetErrorString(cudaGetLastError()));
   return TOR_OK;

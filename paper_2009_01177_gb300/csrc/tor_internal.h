@@ -108,7 +108,7 @@ int launch_bounds_single(const double *O, int k, int ld, int layout, double tol,
                          cudaStream_t s);
 int launch_propose_plain(const double *marg, int M, int C, int words, unsigned long long seed,
                          unsigned long long step, unsigned long long *prop, double *logq_prop, cudaStream_t s);
-int launch_accept(int C, int M, int words, double logdet_sigma, const tor_result *tr,
+int launch_accept(int C, int M, int words, int k_cap, double logdet_sigma, const tor_result *tr,
                   const unsigned long long *prop, const double *logq_prop, unsigned long long *pat, double *logp,
                   double *logq, int *accepted, unsigned long long seed, unsigned long long step, cudaStream_t s);
 int mlp_modes(const tor_mlp *m);

@@ -45,23 +45,24 @@ const Binom &host_binom() {
   return b;
 }
 
-// the next smaller mask with the same popcount: drop the trailing block of c
-// ones, then the lowest remaining one (bit p) moves down by one place and the c
-// ones go right below it, which is x - 2^(p - c - 1) for x the mask without
-// them.  Undefined for the smallest mask of a level (no lower mask exists).
+// The next smaller mask with the same popcount.  Masks of one popcount in
+// decreasing order are their complements in increasing order, so the answer is
+// the complement of the smallest larger word with as many ones as ~mask (the
+// ones-moving identity of HAKMEM item 175, Gosper): adding the lowest set bit
+// carries through the lowest block of ones, leaving one 1 just above the
+// block, and the block's other ones return at the bottom.  Undefined for the
+// smallest mask of a level (all its ones at the bottom: no smaller mask).
 __host__ __device__ inline unsigned long long next_mask(unsigned long long mask) {
+  const unsigned long long y = ~mask;
+  const unsigned long long low = y & (0ull - y);  // lowest set bit of y
+  const unsigned long long r = y + low;           // the block of ones carried up by one place
 #if defined(__CUDA_ARCH__)
-  const int c = __ffsll((long long)~mask) - 1;  // trailing ones
+  const int p = __ffsll((long long)low) - 1;
 #else
-  const int c = __builtin_ctzll(~mask);
+  const int p = __builtin_ctzll(low);
 #endif
-  const unsigned long long x = mask - ((1ull << c) - 1ull);
-#if defined(__CUDA_ARCH__)
-  const int p = __ffsll((long long)x) - 1;
-#else
-  const int p = __builtin_ctzll(x);
-#endif
-  return x - (1ull << (p - c - 1));
+  const unsigned long long back = ((y ^ r) >> 2) >> p;  // block length minus one ones, at the bottom
+  return ~(r | back);
 }
 
 // the r-th (0-based) mask of popcount m over k bits, in decreasing order

@@ -12,7 +12,11 @@
 // Every random draw is Philox4x32-10 at (seed; step, chain, j): j < M are
 // the proposal's mode draws, j = M the acceptance draw.  A chain whose
 // current log p is -inf (not yet initialised) accepts any proposal with
-// p(S') > 0.  Proposals with Tor <= 0 or a failed instance are rejected.
+// p(S') > 0.  A proposal whose p(S') is not known to the requested tolerance
+// is rejected and says why in `accepted` (negative codes), so that callers
+// can count every such rejection: -1 more clicks than the cap (not
+// evaluated), -2 the Torontonian missed the tolerance in the most precise tier
+// that holds it (TOR_EPREC), -3 any other failed evaluation or Tor <= 0.
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cmath>
@@ -39,7 +43,7 @@ __global__ void k_propose_plain(const double *__restrict__ marg, int M, int C, i
   logq_prop[c] = lq;
 }
 
-__global__ void k_accept(int C, int M, int words, double logdet_sigma, const tor_result *__restrict__ tr,
+__global__ void k_accept(int C, int M, int words, int k_cap, double logdet_sigma, const tor_result *__restrict__ tr,
                          const unsigned long long *__restrict__ prop, const double *__restrict__ logq_prop,
                          unsigned long long *__restrict__ pat, double *__restrict__ logp, double *__restrict__ logq,
                          int *__restrict__ accepted, unsigned long long seed, unsigned long long step) {
@@ -49,6 +53,9 @@ __global__ void k_accept(int C, int M, int words, double logdet_sigma, const tor
   const double tor = r.hi + r.lo;
   const double lp_new = (r.status == TOR_OK && tor > 0.0) ? log(tor) - 0.5 * logdet_sigma : -INFINITY;
   const double lp_old = logp[c];
+  int clicks = 0;
+  for (int i = 0; i < words; ++i) clicks += __popcll(prop[(size_t)c * words + i]);
+  const int failed = (k_cap > 0 && clicks > k_cap) ? -1 : (r.status == TOR_EPREC) ? -2 : -3;
   bool acc = false;
   if (lp_new > -INFINITY) {
     if (lp_old == -INFINITY) {
@@ -64,7 +71,7 @@ __global__ void k_accept(int C, int M, int words, double logdet_sigma, const tor
     logp[c] = lp_new;
     logq[c] = logq_prop[c];
   }
-  accepted[c] = acc ? 1 : 0;
+  accepted[c] = acc ? 1 : (lp_new > -INFINITY ? 0 : failed);
 }
 
 int launch_propose_plain(const double *marg, int M, int C, int words, unsigned long long seed,
@@ -73,10 +80,10 @@ int launch_propose_plain(const double *marg, int M, int C, int words, unsigned l
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_accept(int C, int M, int words, double logdet_sigma, const tor_result *tr,
+int launch_accept(int C, int M, int words, int k_cap, double logdet_sigma, const tor_result *tr,
                   const unsigned long long *prop, const double *logq_prop, unsigned long long *pat, double *logp,
                   double *logq, int *accepted, unsigned long long seed, unsigned long long step, cudaStream_t s) {
-  k_accept<<<(C + 127) / 128, 128, 0, s>>>(C, M, words, logdet_sigma, tr, prop, logq_prop, pat, logp, logq, accepted,
+  k_accept<<<(C + 127) / 128, 128, 0, s>>>(C, M, words, k_cap, logdet_sigma, tr, prop, logq_prop, pat, logp, logq, accepted,
                                            seed, step);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

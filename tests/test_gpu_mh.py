@@ -88,7 +88,7 @@ def test_plain_step_replays_on_cpu(ctx):
         if abs(lu - la) < 1e-6:
             continue                          # a near-tie: either decision is right
         expect = lu < la
-        assert bool(acc[c]) == expect, c
+        assert (acc[c] == 1) == expect and acc[c] in (0, 1), c
         assert after[c] == (code if expect else before[c])
         checked += 1
     assert checked > 0.95 * C
@@ -142,11 +142,17 @@ def test_click_cap_targets_the_conditional_distribution(ctx):
     p_cond = np.where(clicks <= k_cap, p, 0.0)
     p_cond /= p_cond.sum()
     ch = Chains(st, 8192)
+    capped = 0
     for step in range(40):
         ctx.sample_step(ch.O, ch.logdet, ch.pat, ch.logp, ch.logq, ch.acc, 91, step,
                         marg_p=ch.marg, prec="auto", tol=1e-9, k_cap=k_cap)
         codes = ch.pat[:, 0].cpu().numpy()
         # a chain holds its initial empty pattern until a proposal within the cap is accepted
         assert clicks[codes].max() <= k_cap
+        # every rejection says why: the Metropolis test (0) or the cap (-1); nothing failed
+        acc = ch.acc.cpu().numpy()
+        assert set(np.unique(acc)) <= {-1, 0, 1}
+        capped += int((acc == -1).sum())
+    assert capped > 0
     freq = np.bincount(codes, minlength=1 << M) / ch.C
     assert 0.5 * np.abs(freq - p_cond).sum() < 0.05

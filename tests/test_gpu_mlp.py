@@ -88,6 +88,59 @@ def test_gradients_match_reference(ctx, cuda_lib, M, H):
     net.close()
 
 
+def test_gradients_per_entry_with_all_units_active(ctx, cuda_lib):
+    # small weights and positive hidden biases keep every pre-activation far from the ReLU
+    # kink, so the GPU and the reference gate the same units and every entry can be bounded:
+    # the logits carry at most 2^-6 of their magnitude sum (forward bound above), which
+    # moves dL/dl by at most w/4 of that; four BF16 roundings (2^-9 each) on the way back
+    # stay within 2^-6 of the backward pass on magnitudes seeded with that extra error.
+    M, H, B = 12, 64, 256
+    net = cuda_lib.MLP(ctx, M, H, seed=8)
+    parts = made.unflatten(made.random_theta(M, H, 11, scale=0.3), M, H)
+    for i in (1, 3, 5):
+        parts[i] = np.full(H, 3.0)
+    net.set_params(made.flatten(parts))
+    th32 = net.get_params(0).astype(np.float64)
+    X = rand_patterns(B, M, 12)
+    assert min(z.min() for z in made.preactivations(th32, X, M, H)) > 1.0     # all active, with margin
+    w = np.random.default_rng(13).random(B) + 0.05
+    net.grad(pack_patterns(X, M).cuda(), torch.tensor(w, dtype=torch.float32, device="cuda"))
+    g = net.get_params(1).astype(np.float64)
+    _, g_ref = made.loss_and_grad(th32, X, w, M, H)
+    wn = w / w.sum()
+    dl_err = wn[:, None] * 2.0 ** -8 * made.magnitude_logits(th32, X, M, H)
+    bound = 2.0 ** -6 * made.grad_magnitude(th32, X, w, M, H) + made.grad_magnitude(th32, X, w, M, H, dl_err) \
+        - made.grad_magnitude(th32, X, w, M, H) + 1e-9
+    assert np.all(np.abs(g - g_ref) <= bound)
+    mk = net.get_params(2)
+    assert np.all(g[mk == 0] == 0)                       # masked entries have no gradient
+    net.close()
+
+
+def test_adam_update_matches_reference(ctx, cuda_lib):
+    # the optimizer arithmetic alone: each step's update of the FP32 master weights against
+    # the FP64 masked Adam step of the oracle, given the gradient the GPU computed for it
+    M, H, B, lr = 10, 64, 128, 1e-3
+    net = cuda_lib.MLP(ctx, M, H, seed=9)
+    net.set_params(made.random_theta(M, H, 14, scale=1.0))
+    mask = net.get_params(2).astype(np.float64)
+    X = pack_patterns(rand_patterns(B, M, 15), M).cuda()
+    w = torch.rand(B, device="cuda", dtype=torch.float32) + 0.05
+    theta = net.get_params(0).astype(np.float64)
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    for t in range(1, 5):
+        net.train_step(X, w, lr=lr)
+        g = net.get_params(1).astype(np.float64)
+        new = net.get_params(0).astype(np.float64)
+        ref, m, v = made.adam_step(theta, g, m, v, t, lr, mask)
+        # FP32 arithmetic: the update (about lr) to a few parts in 1e6, the weight to its rounding
+        assert np.all(np.abs(new - ref) <= 1e-5 * lr + 2.0 ** -22 * np.abs(ref)), t
+        assert np.all(new[mask == 0] == 0)
+        theta = new
+    net.close()
+
+
 def test_sampling_matches_its_own_density(ctx, cuda_lib):
     M, H, B = 6, 64, 16384
     net = cuda_lib.MLP(ctx, M, H, seed=4)
