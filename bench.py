@@ -604,6 +604,27 @@ def run_mh(args):
             causes[label] = {"over_k_cap": c[0], "missed_tol": c[1], "failed": c[2], "proposals": steps * ch["C"]}
         return float(acc) / steps
 
+    def run_da(ch, steps, seed, net, record=None, t0=0, k_cap=0, label=None):
+        """steps delayed-acceptance steps (plain proposals screened by the network's density,
+        the exact Torontonian only for the survivors); the mean acceptance."""
+        if "logs" not in ch:          # the surrogate's log density of the current states
+            ch["logs"] = net.logq(ch["pat"])
+        acc = torch.zeros((), dtype=torch.float64, device="cuda")
+        cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+        for s_ in range(steps):
+            ctx.sample_step_da(ch["O"], ch["logdet"], ch["pat"], ch["logp"], ch["logq"], ch["logs"], ch["acc"], seed,
+                               t0 + s_, marg_p=ch["marg"], surrogate=net, prec="auto", tol=tol, k_cap=k_cap)
+            a = ch["acc"]
+            acc += (a == 1).double().mean()
+            cnt += torch.stack([(a == -1).sum(), (a == -2).sum(), (a == -3).sum(), (a == -4).sum()])
+            if record is not None:
+                record.append(ch["pat"].clone())
+        if label is not None:
+            c = cnt.tolist()
+            causes[label] = {"over_k_cap": c[0], "missed_tol": c[1], "failed": c[2], "screened_out": c[3],
+                             "proposals": steps * ch["C"]}
+        return float(acc) / steps
+
     def train(net, pats, w, iters, batch, lr, val=None, val_w=None, resample=False):
         """Adam on the weighted NLL; with val, keep the parameters of best validation NLL
         (weighted by val_w when given).  resample: draw each batch with probability
@@ -685,14 +706,15 @@ def run_mh(args):
                             val=Pis[vi].contiguous(), val_w=wt[vi].double().contiguous(), resample=True)
     res = {}
     steps = max(8, 4 * args.steps)
-    for name, prop in (("plain", None), ("learned", net), ("learned_is", net_is)):
+    for name, prop in (("plain", None), ("learned", net), ("learned_is", net_is), ("delayed_acceptance", net)):
         progress(f"race: {name}")
         chn = chains(st)
-        run(chn, 3, 7, prop, k_cap=k_cap)
+        step_fn = (lambda *a, **kw: run_da(*a[:3], net, *a[4:], **kw)) if name == "delayed_acceptance" else run
+        step_fn(chn, 3, 7, prop, k_cap=k_cap)
         series = []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        acc = run(chn, steps, 7, prop, record=series, t0=100, k_cap=k_cap, label=name)
+        acc = step_fn(chn, steps, 7, prop, record=series, t0=100, k_cap=k_cap, label=name)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         ess = _ess_geyer(np.stack([_click_counts(p) for p in series]).astype(float))
@@ -705,6 +727,12 @@ def run_mh(args):
            "learned": res["learned"],
            "speedup_accepted": res["learned"]["accepted_samples_per_s"] / res["plain"]["accepted_samples_per_s"],
            "speedup_ess": res["learned"]["ess_per_s"] / max(res["plain"]["ess_per_s"], 1e-30),
+           "delayed_acceptance": dict(res["delayed_acceptance"], note="plain proposals screened by the "
+                                      "learned network's density; exact Torontonians only for the survivors"),
+           "speedup_ess_delayed_acceptance": res["delayed_acceptance"]["ess_per_s"] / max(res["plain"]["ess_per_s"],
+                                                                                          1e-30),
+           "speedup_accepted_delayed_acceptance": res["delayed_acceptance"]["accepted_samples_per_s"] /
+                                                  res["plain"]["accepted_samples_per_s"],
            "validation_nll": {"plain_proposal": nll_plain, "learned": nll_learned},
            "importance_weighted": {"pairs": int(X.shape[0]), "weight_ess": ess_is, "scoring_s": t_is,
                                    "weighted_validation_nll": {"plain_proposal": nll_is0, "learned_is": nll_is},

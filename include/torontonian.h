@@ -422,6 +422,29 @@ int gbs_sample_step(tor_ctx *ctx, const double *O, int M, int ld, double logdet_
                     double *logp, double *logq, int *accepted, uint64_t seed, uint64_t step,
                     int prec, double tol, int k_cap, cudaStream_t stream);
 
+/*
+ * gbs_sample_step_da: one Metropolis-Hastings step of C chains targeting
+ * p(S) = Tor(O_S) / sqrt(det Sigma) (Eq. 1, the paper's MCMC use, Sec. 7.1.1)
+ * by delayed acceptance (Christen & Fox 2005) with the network as a cheap
+ * surrogate of p: the plain proposal S' (as in gbs_sample_step) first passes
+ * a test on the surrogate, min(1, s(S') q(S) / (s(S) q(S'))), Philox draw
+ * j = M; only the proposals that pass have their exact Torontonian computed,
+ * and a second test, min(1, p(S') s(S) / (p(S) s(S'))), draw j = M + 1,
+ * corrects the surrogate's error exactly, so the chain targets p whatever the
+ * surrogate.  Acceptance always rests on the exact Torontonian.
+ *   surrogate  a tor_mlp over the same M (s = its normalised density q_net).
+ *   logs       dev  C doubles: ln s of the current states (in/out; refresh
+ *              with tor_mlp_logq after retraining the network).
+ *   accepted   as gbs_sample_step, plus -4: rejected by the surrogate's test
+ *              (no Torontonian computed).  An uninitialised chain (logp = -inf)
+ *              skips the surrogate's test.
+ * The other arguments are those of gbs_sample_step (marg_p required).
+ */
+int gbs_sample_step_da(tor_ctx *ctx, const double *O, int M, int ld, double logdet_sigma, const double *marg_p,
+                       tor_mlp *surrogate, int C, uint64_t *patterns, double *logp, double *logq, double *logs,
+                       int *accepted, uint64_t seed, uint64_t step, int prec, double tol, int k_cap,
+                       cudaStream_t stream);
+
 /* -------------------------------------------------------------- utilities */
 
 /* Kernel timing: when `on`, the walk kernel of every later call is bracketed

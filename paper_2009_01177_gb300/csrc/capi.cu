@@ -729,6 +729,42 @@ int gbs_sample_step(tor_ctx *ctx, const double *O, int M, int ld, double logdet_
   return TOR_OK;
 }
 
+int gbs_sample_step_da(tor_ctx *ctx, const double *O, int M, int ld, double logdet_sigma, const double *marg_p,
+                       tor_mlp *surrogate, int C, uint64_t *patterns, double *logp, double *logq, double *logs,
+                       int *accepted, uint64_t seed, uint64_t step, int prec, double tol, int k_cap, cudaStream_t s) {
+  if (!ctx) return fail(TOR_EINVAL, "null context");
+  if (M < 1 || M > 128) return fail(TOR_EINVAL, "M = %d outside [1, 128]", M);
+  if (C < 0) return fail(TOR_EINVAL, "C = %d < 0", C);
+  if (C == 0) return TOR_OK;
+  if (!O || !marg_p || !surrogate || !patterns || !logp || !logq || !logs || !accepted)
+    return fail(TOR_EINVAL, "null pointer");
+  if (tor::mlp_modes(surrogate) != M) return fail(TOR_EINVAL, "surrogate network has a different M");
+  CK(cudaSetDevice(ctx->device));
+  const int words = (M + 63) / 64;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t b_prop = al(sizeof(uint64_t) * words * (size_t)C), b_d = al(sizeof(double) * (size_t)C),
+               b_res = al(sizeof(tor_result) * (size_t)C);
+  int rc;
+  if ((rc = ensure(ctx, ctx->mh, 2 * b_prop + 2 * b_d + b_res))) return rc;
+  unsigned char *base = (unsigned char *)ctx->mh.p;
+  unsigned long long *prop = (unsigned long long *)base;
+  unsigned long long *eval = (unsigned long long *)(base + b_prop);
+  double *lq_prop = (double *)(base + 2 * b_prop);
+  double *ls_prop = (double *)(base + 2 * b_prop + b_d);
+  tor_result *res = (tor_result *)(base + 2 * b_prop + 2 * b_d);
+  if (tor::launch_propose_plain(marg_p, M, C, words, seed, step, prop, lq_prop, s))
+    return fail(TOR_ECUDA, "proposal: %s", cudaGetErrorString(cudaGetLastError()));
+  if ((rc = tor_mlp_logq(surrogate, (const uint64_t *)prop, C, ls_prop, s))) return rc;
+  if (tor::launch_screen(C, M, words, k_cap, prop, lq_prop, ls_prop, logp, logq, logs, eval, accepted, seed, step, s))
+    return fail(TOR_ECUDA, "screen: %s", cudaGetErrorString(cudaGetLastError()));
+  if ((rc = batch_patterns(ctx, O, M, ld, (const uint64_t *)eval, C, prec, tol, s, res, k_cap > 0 ? k_cap : -1)))
+    return rc;
+  if (tor::launch_accept_da(C, M, words, logdet_sigma, res, prop, lq_prop, ls_prop, (unsigned long long *)patterns,
+                            logp, logq, logs, accepted, seed, step, s))
+    return fail(TOR_ECUDA, "accept: %s", cudaGetErrorString(cudaGetLastError()));
+  return TOR_OK;
+}
+
 int tor_bounds(tor_ctx *ctx, const double *const *O, const int *k, const int *ld, int n, int layout,
                double tol, cudaStream_t s, tor_bound *out) {
   if (!ctx) return fail(TOR_EINVAL, "null context");

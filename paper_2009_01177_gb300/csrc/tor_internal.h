@@ -111,6 +111,14 @@ int launch_propose_plain(const double *marg, int M, int C, int words, unsigned l
 int launch_accept(int C, int M, int words, int k_cap, double logdet_sigma, const tor_result *tr,
                   const unsigned long long *prop, const double *logq_prop, unsigned long long *pat, double *logp,
                   double *logq, int *accepted, unsigned long long seed, unsigned long long step, cudaStream_t s);
+int launch_screen(int C, int M, int words, int k_cap, const unsigned long long *prop, const double *logq_prop,
+                  const double *logs_prop, const double *logp, const double *logq, const double *logs,
+                  unsigned long long *eval, int *accepted, unsigned long long seed, unsigned long long step,
+                  cudaStream_t s);
+int launch_accept_da(int C, int M, int words, double logdet_sigma, const tor_result *tr,
+                     const unsigned long long *prop, const double *logq_prop, const double *logs_prop,
+                     unsigned long long *pat, double *logp, double *logq, double *logs, int *accepted,
+                     unsigned long long seed, unsigned long long step, cudaStream_t s);
 int mlp_modes(const tor_mlp *m);
 // store a message for tor_last_error() on the calling thread; returns code
 int record_error(int code, const char *msg);

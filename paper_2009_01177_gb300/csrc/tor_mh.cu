@@ -74,6 +74,83 @@ __global__ void k_accept(int C, int M, int words, int k_cap, double logdet_sigma
   accepted[c] = acc ? 1 : (lp_new > -INFINITY ? 0 : failed);
 }
 
+// Delayed acceptance (Christen & Fox 2005) with a surrogate density s (the
+// MADE network's log q): a plain proposal S' first passes a test on the
+// surrogate, min(1, s(S') q(S) / (s(S) q(S'))) with draw j = M; only then is
+// its exact p(S') computed, and the second test min(1, p(S') s(S) / (p(S) s(S')))
+// with draw j = M + 1 corrects the surrogate's error exactly, so the chain
+// still targets p.  Screened-out proposals (and those over the click cap) are
+// replaced by the empty pattern in `eval`, whose Torontonian costs nothing.
+__global__ void k_screen(int C, int M, int words, int k_cap, const unsigned long long *__restrict__ prop,
+                         const double *__restrict__ logq_prop, const double *__restrict__ logs_prop,
+                         const double *__restrict__ logp, const double *__restrict__ logq,
+                         const double *__restrict__ logs, unsigned long long *__restrict__ eval,
+                         int *__restrict__ accepted, unsigned long long seed, unsigned long long step) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  int clicks = 0;
+  for (int i = 0; i < words; ++i) clicks += __popcll(prop[(size_t)c * words + i]);
+  int code = 1;                      // 1: evaluate exactly
+  if (k_cap > 0 && clicks > k_cap) {
+    code = -1;
+  } else if (logp[c] > -INFINITY) {  // an initialised chain: the surrogate's test first
+    const double log_alpha = (logs_prop[c] - logs[c]) + (logq[c] - logq_prop[c]);
+    const double u = philox_uniform(seed, step, (uint32_t)c, (uint32_t)M);
+    if (!(log(u) < log_alpha)) code = -4;
+  }
+  for (int i = 0; i < words; ++i) eval[(size_t)c * words + i] = (code == 1) ? prop[(size_t)c * words + i] : 0ull;
+  accepted[c] = code;
+}
+
+__global__ void k_accept_da(int C, int M, int words, double logdet_sigma, const tor_result *__restrict__ tr,
+                            const unsigned long long *__restrict__ prop, const double *__restrict__ logq_prop,
+                            const double *__restrict__ logs_prop, unsigned long long *__restrict__ pat,
+                            double *__restrict__ logp, double *__restrict__ logq, double *__restrict__ logs,
+                            int *__restrict__ accepted, unsigned long long seed, unsigned long long step) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  if (accepted[c] != 1) return;  // over the cap (-1) or screened out by the surrogate (-4)
+  const tor_result r = tr[c];
+  const double tor = r.hi + r.lo;
+  const double lp_new = (r.status == TOR_OK && tor > 0.0) ? log(tor) - 0.5 * logdet_sigma : -INFINITY;
+  const double lp_old = logp[c];
+  bool acc = false;
+  if (lp_new > -INFINITY) {
+    if (lp_old == -INFINITY) {
+      acc = true;
+    } else {
+      const double log_alpha = (lp_new - lp_old) + (logs[c] - logs_prop[c]);
+      const double u = philox_uniform(seed, step, (uint32_t)c, (uint32_t)(M + 1));
+      acc = log(u) < log_alpha;
+    }
+  }
+  if (acc) {
+    for (int i = 0; i < words; ++i) pat[(size_t)c * words + i] = prop[(size_t)c * words + i];
+    logp[c] = lp_new;
+    logq[c] = logq_prop[c];
+    logs[c] = logs_prop[c];
+  }
+  accepted[c] = acc ? 1 : (lp_new > -INFINITY ? 0 : (r.status == TOR_EPREC ? -2 : -3));
+}
+
+int launch_screen(int C, int M, int words, int k_cap, const unsigned long long *prop, const double *logq_prop,
+                  const double *logs_prop, const double *logp, const double *logq, const double *logs,
+                  unsigned long long *eval, int *accepted, unsigned long long seed, unsigned long long step,
+                  cudaStream_t s) {
+  k_screen<<<(C + 127) / 128, 128, 0, s>>>(C, M, words, k_cap, prop, logq_prop, logs_prop, logp, logq, logs, eval,
+                                           accepted, seed, step);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_accept_da(int C, int M, int words, double logdet_sigma, const tor_result *tr,
+                     const unsigned long long *prop, const double *logq_prop, const double *logs_prop,
+                     unsigned long long *pat, double *logp, double *logq, double *logs, int *accepted,
+                     unsigned long long seed, unsigned long long step, cudaStream_t s) {
+  k_accept_da<<<(C + 127) / 128, 128, 0, s>>>(C, M, words, logdet_sigma, tr, prop, logq_prop, logs_prop, pat, logp,
+                                              logq, logs, accepted, seed, step);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int launch_propose_plain(const double *marg, int M, int C, int words, unsigned long long seed,
                          unsigned long long step, unsigned long long *prop, double *logq_prop, cudaStream_t s) {
   k_propose_plain<<<(C + 127) / 128, 128, 0, s>>>(marg, M, C, words, seed, step, prop, logq_prop);

@@ -119,6 +119,8 @@ SIGNATURES = {
     "tor_mlp_sample": (_I, [_VP, _I, _U64, _U64, _VP, _VP, _VP]),
     "gbs_sample_step": (_I, [_VP, _VP, _I, _I, _D, _VP, _VP, _I, _VP, _VP, _VP, _VP, _U64, _U64, _I, _D, _I,
                              _VP]),
+    "gbs_sample_step_da": (_I, [_VP, _VP, _I, _I, _D, _VP, _VP, _I, _VP, _VP, _VP, _VP, _VP, _U64, _U64, _I,
+                                _D, _I, _VP]),
     "tor_autotune": (_I, [_VP, _I, _I, ctypes.c_char_p, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "tor_set_timing": (_I, [_VP, _I]),
     "tor_walk_time": (_I, [_VP, ctypes.POINTER(ctypes.c_float)]),
@@ -339,6 +341,18 @@ class Context:
                                         logp.data_ptr(), logq.data_ptr(), accepted.data_ptr(),
                                         seed & 0xFFFFFFFFFFFFFFFF, step & 0xFFFFFFFFFFFFFFFF, _PREC[prec], tol,
                                         int(k_cap), _stream(stream)))
+
+    def sample_step_da(self, Ofull: torch.Tensor, logdet_sigma: float, patterns: torch.Tensor, logp: torch.Tensor,
+                       logq: torch.Tensor, logs: torch.Tensor, accepted: torch.Tensor, seed: int, step: int,
+                       marg_p, surrogate, prec: str = "auto", tol: float = 1e-10, k_cap: int = 0, stream=None):
+        """gbs_sample_step_da: plain proposals screened by the surrogate network (logs: its log density
+        of the current states, float64 (C,), in/out), the exact Torontonian only for the survivors."""
+        k2, ld = _mat(Ofull)
+        C = patterns.shape[0]
+        _check(self.lib.gbs_sample_step_da(self.h, Ofull.data_ptr(), k2, ld, float(logdet_sigma), marg_p.data_ptr(),
+                                           surrogate.h, C, patterns.data_ptr(), logp.data_ptr(), logq.data_ptr(),
+                                           logs.data_ptr(), accepted.data_ptr(), seed & 0xFFFFFFFFFFFFFFFF,
+                                           step & 0xFFFFFFFFFFFFFFFF, _PREC[prec], tol, int(k_cap), _stream(stream)))
 
     def autotune(self, k: int, prec: str, cache_path: str | None = None):
         """Time chunk depths and launch shapes for k clicks; returns (chunk_bits, blocks_per_sm)."""

@@ -122,7 +122,7 @@ def test_learned_proposal_beats_plain(ctx, cuda_lib):
         for step in range(8):
             a = ch.step(ctx, 5, step, proposal=prop)
             if step:
-                accs.append(a.mean())
+                accs.append((a == 1).mean())
             freq = np.bincount(ch.pat[:, 0].cpu().numpy(), minlength=1 << M) / ch.C
             tvs.append(0.5 * float(np.abs(freq - p).sum()))
         results[name] = (float(np.mean(accs)), tvs)
@@ -156,3 +156,87 @@ def test_click_cap_targets_the_conditional_distribution(ctx):
     assert capped > 0
     freq = np.bincount(codes, minlength=1 << M) / ch.C
     assert 0.5 * np.abs(freq - p_cond).sum() < 0.05
+
+
+# ------------------------------------------------------- delayed acceptance
+class DAChains(Chains):
+    def __init__(self, st, C, net):
+        super().__init__(st, C)
+        self.net = net
+        self.logs = torch.zeros(C, dtype=torch.float64, device="cuda")
+
+    def step_da(self, ctx, seed, step, k_cap=0):
+        ctx.sample_step_da(self.O, self.logdet, self.pat, self.logp, self.logq, self.logs, self.acc, seed, step,
+                           marg_p=self.marg, surrogate=self.net, prec="auto", tol=1e-9, k_cap=k_cap)
+        return self.acc.cpu().numpy()
+
+
+def _surrogate(cuda_lib, ctx, st, seed, scale):
+    """A MADE network started at the plain proposal and then perturbed: a surrogate of p that
+    is deliberately imperfect (the second test has to correct it)."""
+    from oracle import made
+    M = st.M
+    net = cuda_lib.MLP(ctx, M, 32, seed=seed)
+    net.set_marginals(marginals(st))
+    th = net.get_params(0).astype(np.float64)
+    th += scale * made.random_theta(M, 32, seed, scale=1.0) * (net.get_params(2) > 0)
+    net.set_params(th)
+    return net
+
+
+def test_delayed_acceptance_step_replays_on_cpu(ctx, cuda_lib):
+    st = gi.lossy_gbs_state(6, 0.4, 1.0, 0.6, 65)
+    C, seed, M = 256, 4321, 6
+    net = _surrogate(cuda_lib, ctx, st, 3, 0.5)
+    ch = DAChains(st, C, net)
+    acc0 = ch.step_da(ctx, seed, 0)           # initialise: uninitialised chains skip the first test
+    assert np.all(acc0 == 1)
+    allx = ((np.arange(1 << M)[:, None] >> np.arange(M)[None, :]) & 1).astype(np.float64)
+    logs_all = net.logq(pack_patterns(allx, M).cuda()).cpu().numpy()   # the surrogate, every pattern
+    before = ch.pat[:, 0].cpu().numpy().copy()
+    assert np.allclose(ch.logs.cpu().numpy(), logs_all[before])
+    lp_before, lq_before = ch.logp.cpu().numpy().copy(), ch.logq.cpu().numpy().copy()
+    acc = ch.step_da(ctx, seed, 1)
+    after = ch.pat[:, 0].cpu().numpy()
+    marg = marginals(st)
+    checked = screened = 0
+    for c in range(C):
+        us = [philox_ref.uniform(seed, 1, c, j) for j in range(M)]
+        prop = [1 if us[j] < marg[j] else 0 for j in range(M)]
+        code = sum(b << j for j, b in enumerate(prop))
+        lq_new = sum(math.log(marg[j]) if prop[j] else math.log1p(-marg[j]) for j in range(M))
+        la1 = (logs_all[code] - logs_all[before[c]]) + (lq_before[c] - lq_new)
+        lu1 = math.log(philox_ref.uniform(seed, 1, c, M))
+        if abs(lu1 - la1) < 1e-6:
+            continue
+        if not lu1 < la1:                     # screened out: no Torontonian, the chain stays
+            assert acc[c] == -4 and after[c] == before[c], c
+            screened += 1
+            continue
+        p_new = sum(oracle.prob(st.O, prop, threads=1)[:2])
+        la2 = (math.log(p_new) - lp_before[c]) + (logs_all[before[c]] - logs_all[code])
+        lu2 = math.log(philox_ref.uniform(seed, 1, c, M + 1))
+        if abs(lu2 - la2) < 1e-6:
+            continue
+        expect = lu2 < la2
+        assert acc[c] == (1 if expect else 0), c
+        assert after[c] == (code if expect else before[c])
+        checked += 1
+    assert checked + screened > 0.95 * C and screened > 0 and checked > 0
+    net.close()
+
+
+def test_delayed_acceptance_targets_p_whatever_the_surrogate(ctx, cuda_lib):
+    # a poor surrogate costs acceptance, never correctness: the exact second test makes the
+    # chain reversible for p (Christen and Fox 2005)
+    st = gi.lossy_gbs_state(5, 0.5, 1.1, 0.7, 62)
+    p = exact_probs(st)
+    net = _surrogate(cuda_lib, ctx, st, 4, 2.0)
+    ch = DAChains(st, 8192, net)
+    codes_seen = set()
+    for step in range(60):
+        codes_seen |= set(np.unique(ch.step_da(ctx, 78, step)).tolist())
+    freq = np.bincount(ch.pat[:, 0].cpu().numpy(), minlength=1 << st.M) / ch.C
+    assert 0.5 * np.abs(freq - p).sum() < 0.05
+    assert codes_seen <= {-4, 0, 1} and -4 in codes_seen
+    net.close()
