@@ -313,15 +313,15 @@ def run_adaptive(args):
     pat = gi.random_pattern(100, 50, 1003)
     tol = 1e-10
     rng = np.random.default_rng(3)
-    # walked modes per chunk: at k >= 40 a chunk's root eliminates 26+ modes, so
+    # walked modes per chunk: at k >= 40 a chunk's root eliminates 23+ modes, so
     # longer chunks than the k <= 32 defaults keep the root a few percent of the walk
-    r1_of = {"fp64": 16, "dd": 13, "fx128": 13, "fx256": 13}
-    window = 1 << 18                      # chunks per timed launch: 3.4 per thread of the grid
+    r1_of = {"fp64": 16, "dd": 13, "fx128": 13, "fx256": 17}
+    window_of = {"fp64": 1 << 18, "dd": 1 << 18, "fx128": 1 << 18, "fx256": 1 << 17}  # 2.2-4.5 chunks per thread
     out = {"metric": "adaptive precision: routed tier and projected single-GPU runtime (k=40, k=50)",
            "unit": "subset-dets/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
            "config": {"workload": "M=100 synthetic lossy GBS state (r~U[0.8,1.4], Haar U, eta=0.3, seed 3), "
                                   "nested random patterns of k=40 and k=50 clicks; tol=1e-10",
-                      "window_chunks": window, "l2": "inputs resident (the walk reads a 2k x 2k matrix)"}}
+                      "window_chunks": window_of, "l2": "inputs resident (the walk reads a 2k x 2k matrix)"}}
     with ClockSampler(0) as clocks:
         for k in (40, 50):
             Od = torch.from_numpy(gi.select(st.O, pat[:k])).cuda()
@@ -330,6 +330,7 @@ def run_adaptive(args):
             rows = {}
             for prec in dict.fromkeys([routed, "fp64"]):
                 d = k - r1_of[prec]
+                window = window_of[prec]
                 nchunks = 1 << d
                 ms = []
                 for w in range(4):
@@ -811,6 +812,42 @@ def _timed_walks(ctx, Od, prec, reps):
     return ms, tor.TorResult.from_bytes(out.cpu().numpy().tobytes())
 
 
+def k50_projection(ctx, rng_seed=3, windows=2):
+    """Config 3's k = 50 Torontonian (M = 100, r ~ U[0.8, 1.4], eta = 0.3, seed 3): the bound
+    pass routes it, random windows of its chunks are walked at that tier (one warm-up), and the
+    full 2^50-subset runtime is projected from the mean rate."""
+    import math
+    import torch
+    from paper_2009_01177_gb300 import gbs_inputs as gi
+    st = gi.lossy_gbs_state(100, 0.8, 1.4, 0.3, 3)
+    pat = gi.random_pattern(100, 50, 1003)
+    k = 50
+    Od = torch.from_numpy(gi.select(st.O, pat[:k])).cuda()
+    bd = ctx.bounds([Od], tol=1e-10)[0]
+    tier = TIER_NAME[int(bd["tier"])]
+    r1 = {"fp64": 16, "dd": 13, "fx128": 13, "fx256": 17}[tier]
+    window = 1 << 17
+    d = k - r1
+    rng = np.random.default_rng(rng_seed)
+    ms = []
+    for w in range(windows + 1):
+        c0 = int(rng.integers(0, (1 << d) // window)) * window
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.chunks(Od, d, c0, c0 + window, prec=tier)
+        e1.record()
+        torch.cuda.synchronize()
+        if w:
+            ms.append(e0.elapsed_time(e1))
+    rate = window * (1 << r1) / (float(np.mean(ms)) * 1e-3)
+    return {"workload": "k=50 pattern (100x100 O_S) of the M=100 state r~U[0.8,1.4], eta=0.3, seed 3",
+            "routed_tier": tier, "bits_needed": float(bd["bits_needed"]),
+            "log2_tmax": float(bd["log_tmax"]) / math.log(2), "chunk_bits": d, "window_chunks": window,
+            "windows_ms": [round(x, 1) for x in ms], "subset_dets_per_s": rate,
+            "projected_full_s": 2.0 ** k / rate,
+            "paper_context_s": {"128-bit, 39,286 TaihuLight nodes": 73773, "256-bit, same": 170891}}
+
+
 def run_single(args):
     """One Torontonian per step, routed by the bound pass to the tier that resolves it and
     checked against tol; on N > 1 ranks the chunks of that one Torontonian are split."""
@@ -899,6 +936,8 @@ def run_single(args):
                 "note": "FP64 tier timed on the same instance; its error bound exceeds |Tor| at this "
                         "kappa, so it is a kernel-quality figure, not a Torontonian"}
 
+    k50 = None if args.no_k50 else k50_projection(ctx)
+
     units = float(2 ** k) * args.steps
     value = units / total_s
     walk_avg = float(np.mean(walk_ms))
@@ -942,6 +981,7 @@ def run_single(args):
         "gpu_launches": 4 * args.steps,
         "roofline": roofline,
         "fp64_walk": fp64,
+        "k50_projection": k50,
         "paper_equivalent": {"tflops": paper_flops(k) / (walk_avg * 1e-3) / 1e12, "flops_per_launch": paper_flops(k),
                              "note": "the paper's FLOP count of Eq. tflops (a fresh complex solve per "
                                      "subset) over the walk time"},
@@ -1020,6 +1060,7 @@ def main():
                          "on the a-posteriori bound) or an explicit tier")
     ap.add_argument("--tol", type=float, default=1e-10, help="relative tolerance every result must meet")
     ap.add_argument("--no-fp64", action="store_true", help="single mode: skip the secondary FP64 walk timing")
+    ap.add_argument("--no-k50", action="store_true", help="single mode: skip the k = 50 runtime projection")
     ap.add_argument("--n", type=int, default=4096, help="patterns (batch) or chains (mh)")
     ap.add_argument("--mh-tol", type=float, default=1e-8, help="mh mode: tolerance of every exact Torontonian")
     ap.add_argument("--chunk-bits", type=int, default=None,

@@ -128,6 +128,13 @@ int walk_grid(tor_ctx *ctx, int tier) {
 #define TOR_BATCH_R1_F64 16
 #endif
 
+// walked modes per chunk of a 256-bit batch item: at 12 the chunk roots of a
+// k = 30 instance add about 9 % to its walk, at 16 about 1 % (the
+// single-instance autotuner picks 16 at k = 32)
+#ifndef TOR_BATCH_R1_FX256
+#define TOR_BATCH_R1_FX256 16
+#endif
+
 #ifndef TOR_TAIL_SPLIT
 #define TOR_TAIL_SPLIT 1
 #endif
@@ -221,7 +228,7 @@ int tor_create(tor_ctx **out, int device) {
     c->r1_table[TOR_PREC_FP64][kk] = (unsigned char)(kk < TOR_BATCH_R1_F64 ? kk : TOR_BATCH_R1_F64);
     c->r1_table[TOR_PREC_DD][kk] = (unsigned char)(kk < 12 ? kk : 12);
     c->r1_table[TOR_PREC_FX128][kk] = (unsigned char)(kk < 12 ? kk : 12);
-    c->r1_table[TOR_PREC_FX256][kk] = (unsigned char)(kk < 12 ? kk : 12);
+    c->r1_table[TOR_PREC_FX256][kk] = (unsigned char)(kk < TOR_BATCH_R1_FX256 ? kk : TOR_BATCH_R1_FX256);
   }
   cudaError_t e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess) {
