@@ -70,6 +70,17 @@ __device__ __forceinline__ void fx9_columns(long long (&col)[11], const fx9 &a, 
   }
 }
 
+// the same for a b whose b has limbs 0..JB only (the rest zero)
+template <int JB>
+__device__ __forceinline__ void fx9_columns_short(long long (&col)[11], const fx9 &a, const fx9 &b) {
+#pragma unroll
+  for (int c = 6; c <= 16; ++c) {
+#pragma unroll
+    for (int i = (c > 8 ? c - 8 : 0); i <= (c < 8 ? c : 8); ++i)
+      if (c - i <= JB) fx9_mac(col[c - 6], a.l[i], b.l[c - i]);
+  }
+}
+
 // column accumulators: column 6 starts at the rounding bias, columns 7..15 at
 // the balanced-carry bias 2^28 plus the limbs of s (if any), column 16 at 0
 __device__ __forceinline__ void fx9_init(long long (&col)[11]) {

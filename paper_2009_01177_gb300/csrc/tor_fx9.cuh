@@ -38,6 +38,9 @@ namespace tor {
 #ifndef FX9_MINB
 #define FX9_MINB 3
 #endif
+#ifndef FX9_DDSEED
+#define FX9_DDSEED 0
+#endif
 
 // entries of the shared-memory mini-stack: a node of RSMEM modes and the chain
 // of its largest non-last descendants (RSMEM - 2, RSMEM - 4, ...)
@@ -190,6 +193,28 @@ __device__ void fx9_walk_chunk(const Src &src, int k, int r1, unsigned long long
       const fx9 det2 = fx9_dot2(a, d, fx9_neg(b), b, ovf);
       const double xd = fx9_to_double(det2);
       if (!(xd > 0.0) || fx9_sign(a) <= 0) A.flags |= ST_NOTPD;  // 2x2 block PD iff a > 0, det > 0
+#if FX9_DDSEED
+      // y = det2^-1/2: a double-double seed of about 100 bits on the FP64 pipe
+      // (det2 = xd + xl exactly to 2^-100, one double-double Newton step from
+      // the FP64 reciprocal square root), then one fixed-point Newton step
+      // y += (y/2)(1 - det2 y^2), whose error term has limbs 0..3 only
+      fx9 y;
+      {
+        const double xl = fx9_to_double(fx9_sub(det2, fx9_from_double(xd, ovf), ovf));
+        const double y0 = xd > 0.0 ? rsqrt_fp64(xd) : 0.0;
+        const double ph = y0 * y0, pl = fma(y0, y0, -ph);
+        const double qh = xd * ph, ql = fma(xd, ph, -qh);
+        const double e0 = (1.0 - qh) - fma(xl, ph, fma(xd, pl, ql));
+        y = fx9_add(fx9_from_double(y0, ovf), fx9_from_double((0.5 * y0) * e0, ovf), ovf);
+        const fx9 y2 = fx9_mul(y, y, ovf);
+        const fx9 e = fx9_fma(one, fx9_neg(det2), y2, ovf);
+        if (e.l[4] | e.l[5] | e.l[6] | e.l[7] | e.l[8]) ovf = 1;  // the seed missed 2^-115: not a PD block
+        long long col[11];
+        fx9_init(col, y);
+        fx9_columns_short<3>(col, fx9_half(y), e);
+        y = fx9_carry(col, ovf);
+      }
+#else
       // y = det2^-1/2: FP64 seed, two Newton steps y += (y/2)(1 - det2 y^2)
       fx9 y = fx9_from_double(xd > 0.0 ? rsqrt_fp64(xd) : 0.0, ovf);
       const fx9 nx = fx9_neg(det2);
@@ -199,6 +224,7 @@ __device__ void fx9_walk_chunk(const Src &src, int k, int r1, unsigned long long
         const fx9 e = fx9_fma(one, nx, y2, ovf);
         y = fx9_fma(y, fx9_half(y), e, ovf);
       }
+#endif
       const fx9 tc = fx9_mul(t, y, ovf);
       if (skip <= 1) A.add(tc, ((k ^ (par + 1)) & 1) != 0);
       if (cur > 0) {
