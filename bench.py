@@ -707,10 +707,11 @@ def run_mh(args):
                             val=Pis[vi].contiguous(), val_w=wt[vi].double().contiguous(), resample=True)
     res = {}
     steps = max(8, 4 * args.steps)
-    for name, prop in (("plain", None), ("learned", net), ("learned_is", net_is), ("delayed_acceptance", net)):
+    for name, prop in (("plain", None), ("learned", net), ("learned_is", net_is), ("delayed_acceptance", net),
+                       ("delayed_acceptance_is", net_is)):
         progress(f"race: {name}")
         chn = chains(st)
-        step_fn = (lambda *a, **kw: run_da(*a[:3], net, *a[4:], **kw)) if name == "delayed_acceptance" else run
+        step_fn = (lambda *a, **kw: run_da(*a[:3], a[3], *a[4:], **kw)) if name.startswith("delayed") else run
         step_fn(chn, 3, 7, prop, k_cap=k_cap)
         series = []
         torch.cuda.synchronize()
@@ -734,6 +735,10 @@ def run_mh(args):
                                                                                           1e-30),
            "speedup_accepted_delayed_acceptance": res["delayed_acceptance"]["accepted_samples_per_s"] /
                                                   res["plain"]["accepted_samples_per_s"],
+           "delayed_acceptance_is": dict(res["delayed_acceptance_is"], note="the same, screened by the network "
+                                         "trained on importance-weighted exact pairs"),
+           "speedup_ess_delayed_acceptance_is": res["delayed_acceptance_is"]["ess_per_s"] /
+                                                max(res["plain"]["ess_per_s"], 1e-30),
            "validation_nll": {"plain_proposal": nll_plain, "learned": nll_learned},
            "importance_weighted": {"pairs": int(X.shape[0]), "weight_ess": ess_is, "scoring_s": t_is,
                                    "weighted_validation_nll": {"plain_proposal": nll_is0, "learned_is": nll_is},
@@ -882,7 +887,11 @@ def run_single(args):
         ctx.set_launch(128, tuned_bps)
         launch_how = "given"
     if world > 1:
-        return run_sharded(args, ctx, Od, k, tier, tuned_d, route, rank, world, dev)
+        # every rank must cut the subsets into the same chunks: rank 0's depth for all
+        import torch.distributed as dist
+        dt = torch.tensor([tuned_d], dtype=torch.int64, device=dev)
+        dist.broadcast(dt, 0)
+        return run_sharded(args, ctx, Od, k, tier, int(dt.item()), route, rank, world, dev)
 
     peak_dfma, clk = ctx.fp64_peak()
     peak_mad = ctx.int_peak()

@@ -263,7 +263,7 @@ int tor_level_kth_mask(int k, int m, uint64_t r, uint64_t *mask);
  * fixed point of Sec. 5.1-5.2), exposed so tests can check the arithmetic bit
  * for bit.  Each operand is n x 9 int32 limbs on the device, value
  * sum_i l_i 2^(29 i - 203) (any limbs below 2^29 in magnitude); the result
- * is n x 9 limbs within 2^28 + 33 of zero whose value is the exact sum of the
+ * is n x 9 limbs in [-2^28, 2^28) whose value is the exact sum of the
  * product columns c >= 6 (limb pairs i + j >= 6) and of s, rounded to nearest
  * at 2^-203 (ties up); ovf_dev[i] = 1 when its magnitude reaches 2^57.  Asynchronous on
  * `stream`; TOR_EINVAL for n < 0 or null pointers. */

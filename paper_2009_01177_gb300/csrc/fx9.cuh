@@ -95,36 +95,6 @@ __device__ __forceinline__ void fx9_init(long long (&col)[11], const fx9 &s) {
   col[10] = 0;
 }
 
-#ifndef FX9_CARRY2
-#define FX9_CARRY2 0
-#endif
-
-#if FX9_CARRY2
-// two parallel passes instead of one serial one: every column is split at bit
-// 29 (balanced) on its own, each limb adds the high part of the column below,
-// and a second split of those small sums leaves carries of a few units, added
-// without a further pass: limbs within 2^28 + 33 of zero, the same value
-__device__ __forceinline__ fx9 fx9_carry(const long long (&col)[11], int &ovf) {
-  int lo[11];
-  long long hi[11];
-#pragma unroll
-  for (int m = 0; m < 11; ++m) {
-    const long long w = (m < 10) ? col[m] : col[m] + FX9_HALF;  // columns 6..15 carry the bias already
-    lo[m] = (int)((unsigned)w & FX9_MASK) - FX9_HALF;
-    hi[m] = w >> 29;
-  }
-  fx9 r;
-  int prev = 0;
-#pragma unroll
-  for (int j = 0; j < 9; ++j) {
-    const long long w2 = (long long)lo[j + 1] + hi[j] + FX9_HALF;
-    r.l[j] = (int)((unsigned)w2 & FX9_MASK) - FX9_HALF + prev;
-    prev = (int)(w2 >> 29);
-  }
-  if ((long long)prev + lo[10] + hi[9] + (hi[10] << 29) != 0) ovf = 1;
-  return r;
-}
-#else
 // balanced carry pass: columns 7..15 -> limbs 0..8; ovf when the result's
 // magnitude reaches 2^57 (a carry out of limb 8, or column 16 non-zero)
 __device__ __forceinline__ fx9 fx9_carry(const long long (&col)[11], int &ovf) {
@@ -139,7 +109,6 @@ __device__ __forceinline__ fx9 fx9_carry(const long long (&col)[11], int &ovf) {
   if ((c + col[10]) != 0) ovf = 1;
   return r;
 }
-#endif
 
 // a b
 __device__ __forceinline__ fx9 fx9_mul(const fx9 &a, const fx9 &b, int &ovf) {
