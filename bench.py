@@ -133,13 +133,19 @@ def walk_ops(r):
     return p, c, rows, e, n + 1
 
 
+# the reciprocal square root's one fixed-point Newton step ends in a product
+# with an error term of four non-zero limbs: limb pairs i + j >= 6 with j <= 3
+MAC_SHORT_PRODUCT = 18
+
+
 def fx256_macs_per_subset(k):
     """Algorithmic limb multiply-adds per subset of the 256-bit-class walk: per subset its
-    pivot (2x2 determinant: 2 products, two Newton steps of the reciprocal square root: 6,
-    the term t y: 1), per non-leaf pivot the coefficients D^-1 (4), per pivot row the
-    vector D^-1 u (4), per Schur entry the rank-2 update (2); each product 60 MACs."""
+    pivot (2x2 determinant: 2 products; the reciprocal square root from a double-double seed:
+    y^2 and det2 y^2, then a short product; the term t y: 1), per non-leaf pivot the
+    coefficients D^-1 (4), per pivot row the vector D^-1 u (4), per Schur entry the rank-2
+    update (2); each full product 60 MACs, the short one 18."""
     p, c, rows, e, n = walk_ops(k)
-    return MAC_PER_PRODUCT * (9 * p + 4 * c + 4 * rows + 2 * e) / n
+    return (MAC_PER_PRODUCT * (5 * p + 4 * c + 4 * rows + 2 * e) + MAC_SHORT_PRODUCT * p) / n
 
 
 def hbm_peak():
@@ -353,6 +359,18 @@ def run_adaptive(args):
             out[f"k{k}"] = {"routed_tier": routed, "bits_needed": bd["bits_needed"],
                             "log2_tmax": bd["log_tmax"] / math.log(2),
                             "log2_kappa_est": bd["log_kappa_est"] / math.log(2), "tiers": rows}
+    if args.full_k40:            # the whole k = 40 Torontonian through the AUTO path, timed and checked
+        Od = torch.from_numpy(gi.select(st.O, pat[:40])).cuda()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = ctx.single(Od, prec="auto", tol=tol)
+        e1.record()
+        torch.cuda.synchronize()
+        s_full = e0.elapsed_time(e1) / 1e3
+        out["k40_full"] = {"s": s_full, "subset_dets_per_s": 2.0 ** 40 / s_full, "tier": TIER_NAME[r.tier],
+                           "tor": r.value, "hi": r.hi, "lo": r.lo, "sum_abs": r.sum_abs, "err_est": r.err_est,
+                           "err_est_over_tor": r.err_est / abs(r.value), "kappa": r.kappa,
+                           "resolved": bool(r.status == 0 and r.err_est <= tol * abs(r.value))}
     out["value"] = out["k40"]["tiers"][out["k40"]["routed_tier"]]["subset_dets_per_s"]
     out["dtype"] = out["k40"]["routed_tier"]
     out["clocks"] = clocks.summary()
@@ -962,9 +980,10 @@ def run_single(args):
                     "peak_source": "measured: independent mad.wide.s32 chains on all SMs (tor_int_peak), "
                                    "the limb product of the 256-bit-class arithmetic",
                     "macs_per_subset": macs,
-                    "derivation": "per subset: 2x2 det 2 + two Newton steps 6 + term 1 products, 0.5 "
-                                  "coefficient sets x 4, 2 pivot rows x 4, 7 Schur entries x 2 = 33 "
-                                  "products of 60 limb MACs (walk over all 2^k subsets)",
+                    "derivation": "per subset: 2x2 det 2 + rsqrt step 2 + term 1 products, 0.5 "
+                                  "coefficient sets x 4, 2 pivot rows x 4, 7 Schur entries x 2 = 29 "
+                                  "products of 60 limb MACs, plus the rsqrt step's 18-MAC short "
+                                  "product (walk over all 2^k subsets); the seed runs on the FP64 pipe",
                     "dram": dram_rate(traffic, walk_avg)}
     else:
         achieved = FLOPS_PER_SUBSET * 2 ** k / (walk_avg * 1e-3) / 1e12
@@ -1070,6 +1089,7 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-10, help="relative tolerance every result must meet")
     ap.add_argument("--no-fp64", action="store_true", help="single mode: skip the secondary FP64 walk timing")
     ap.add_argument("--no-k50", action="store_true", help="single mode: skip the k = 50 runtime projection")
+    ap.add_argument("--full-k40", action="store_true", help="adaptive mode: also run the whole k = 40 Torontonian")
     ap.add_argument("--n", type=int, default=4096, help="patterns (batch) or chains (mh)")
     ap.add_argument("--mh-tol", type=float, default=1e-8, help="mh mode: tolerance of every exact Torontonian")
     ap.add_argument("--chunk-bits", type=int, default=None,

@@ -38,8 +38,11 @@ namespace tor {
 #ifndef FX9_MINB
 #define FX9_MINB 3
 #endif
+// the reciprocal square root's seed: 1 = double-double (about 100 bits) and
+// one fixed-point Newton step (2.28 G subset-dets/s at k = 32), 0 = FP64 and
+// two steps (2.20)
 #ifndef FX9_DDSEED
-#define FX9_DDSEED 0
+#define FX9_DDSEED 1
 #endif
 
 // entries of the shared-memory mini-stack: a node of RSMEM modes and the chain
