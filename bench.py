@@ -276,7 +276,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(per_step),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fixed256",
-            "data": "synthetic", "config": config(k, {"tier": "oracle (256-bit fixed point, CPU)"}),
+            "data": "synthetic", "config": config(k, {"tier": "oracle (256-bit fixed point, CPU)",
+                                                     "l2": "not applicable (host cores)"}),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

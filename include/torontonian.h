@@ -200,7 +200,9 @@ int tor_chunks(tor_ctx *ctx, const double *O, int k, int ld, int layout, int pre
  * double-double up to k = 17).  All calls share the array: calls that
  * overlap on the GPU race and must be serialised by the caller.  The first
  * call on a device looks up the array's address; make it before any stream
- * capture.  Results equal tor_single's for the same tier.
+ * capture.  Every call only enqueues work on `stream` (k = 0 included: its
+ * constant result is written by a kernel).  Results equal tor_single's for
+ * the same tier.
  */
 int tor_single_noalloc(const double *O, int k, int ld, int layout, int prec,
                        cudaStream_t stream, tor_result *out_dev);
