@@ -323,12 +323,20 @@ def run_adaptive(args):
     # walked modes per chunk: at k >= 40 a chunk's root eliminates 23+ modes, so
     # longer chunks than the k <= 32 defaults keep the root a few percent of the walk
     r1_of = {"fp64": 16, "dd": 13, "fx128": 13, "fx256": 17}
-    window_of = {"fp64": 1 << 18, "dd": 1 << 18, "fx128": 1 << 18, "fx256": 1 << 17}  # 2.2-4.5 chunks per thread
+    # each window is whole waves of the resident grid (3 blocks of 128 threads per SM, the
+    # tuned k = 32 launch of every tier), so no partial last wave skews the rate
+    bps, tpb = 3, 128
+    ctx.set_launch(tpb, bps)
+    threads = torch.cuda.get_device_properties(0).multi_processor_count * bps * tpb
+    waves_of = {"fp64": 4, "dd": 4, "fx128": 4, "fx256": 2}
+    window_of = {p: w * threads for p, w in waves_of.items()}
     out = {"metric": "adaptive precision: routed tier and projected single-GPU runtime (k=40, k=50)",
            "unit": "subset-dets/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
            "config": {"workload": "M=100 synthetic lossy GBS state (r~U[0.8,1.4], Haar U, eta=0.3, seed 3), "
                                   "nested random patterns of k=40 and k=50 clicks; tol=1e-10",
-                      "window_chunks": window_of, "l2": "inputs resident (the walk reads a 2k x 2k matrix)"}}
+                      "window_chunks": window_of, "window_waves": waves_of,
+                      "launch": {"threads_per_block": tpb, "blocks_per_sm": bps},
+                      "l2": "inputs resident (the walk reads a 2k x 2k matrix)"}}
     with ClockSampler(0) as clocks:
         for k in (40, 50):
             Od = torch.from_numpy(gi.select(st.O, pat[:k])).cuda()
@@ -341,7 +349,7 @@ def run_adaptive(args):
                 nchunks = 1 << d
                 ms = []
                 for w in range(4):
-                    c0 = int(rng.integers(0, nchunks // window)) * window
+                    c0 = int(rng.integers(0, nchunks - window + 1))
                     if w == 0:                # warm-up window, not timed
                         ctx.chunks(Od, d, c0, c0 + window, prec=prec)
                         torch.cuda.synchronize()

@@ -96,6 +96,15 @@ __device__ __forceinline__ void fx_add_signed(Fx256 &acc, double x, bool neg, in
 #ifndef TOR_RSQRT_CUBIC
 #define TOR_RSQRT_CUBIC 1
 #endif
+// the seed of the reciprocal square root: 2 = the FP64 approximation
+// instruction (measured max relative error 2^-20.05 over [2^-60, 2^60)),
+// 1 = the FP32 one with x and the seed moved between FP64 and FP32 by exponent
+// rebias on the bit patterns, 0 = the FP32 one with conversion instructions.
+// On GB300 the FP64<->FP32 conversions issue to the FP64 pipe: 0 measured
+// 291.9 ms for the k = 32 FP64 walk, 1 275.2 ms and 2 273.9 ms.
+#ifndef TOR_RSQRT_SEED
+#define TOR_RSQRT_SEED 2
+#endif
 // Nodes of at most RSMEM modes live in one shared-memory slot per thread.  A
 // node of r <= RREG + 2 modes has only register-resident children and its
 // last child, which it overwrites in place, so one slot is enough.
@@ -131,11 +140,54 @@ __device__ __forceinline__ void fx_add_signed(Fx256 &acc, double x, bool neg, in
 #endif
 __device__ __forceinline__ double dmul(double a, double b) { return a * b; }
 
+// Which FP64 multiplies of the FP64 walk run on the integer pipes (dmul_i,
+// below) instead of the FP64 pipe, as a bit mask: 1 = the two products of each
+// pivot row v = S_cc^-1 u, 2 = the pivot coefficients S_cc^-1, 4 = the term
+// t y.  GB300 issues 2 FP64 operations per clock per SM but 64 integer ones,
+// so a multiply in about 40 integer instructions costs the SM about as much
+// time as the native one, on pipes the walk otherwise leaves idle.
+#ifndef TOR_F64_IMUL
+#define TOR_F64_IMUL 0
+#endif
+
+// a * b rounded to nearest even, computed with integer instructions: IEEE 754
+// binary64 multiplication of the significands (53 x 53 -> 106 bits from four
+// 32 x 32 -> 64-bit products), normalised by one place and rounded on the
+// dropped bits.  Operands or results outside the normal range (zero,
+// subnormal, infinite, NaN, or an exponent that could overflow or underflow)
+// take the FP64 multiply, so the result is bit-identical to a * b everywhere.
+__device__ __forceinline__ double dmul_i(double a, double b) {
+  const unsigned long long ua = (unsigned long long)__double_as_longlong(a);
+  const unsigned long long ub = (unsigned long long)__double_as_longlong(b);
+  const int ea = (int)(ua >> 52) & 0x7FF, eb = (int)(ub >> 52) & 0x7FF;
+  const int e0 = ea + eb - 1023;  // the result's biased exponent, before normalisation
+  if ((unsigned)(ea - 1) >= 2046u || (unsigned)(eb - 1) >= 2046u || (unsigned)(e0 - 1) >= 2044u) return a * b;
+  const unsigned long long ma = (ua & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned long long mb = (ub & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned a0 = (unsigned)ma, a1 = (unsigned)(ma >> 32), b0 = (unsigned)mb, b1 = (unsigned)(mb >> 32);
+  const unsigned long long p00 = (unsigned long long)a0 * b0;
+  const unsigned long long mid = (unsigned long long)a0 * b1 + (unsigned long long)a1 * b0;  // < 2^54
+  const unsigned long long lo = p00 + (mid << 32);
+  const unsigned long long hi = (unsigned long long)a1 * b1 + (mid >> 32) + (lo < p00 ? 1ull : 0ull);
+  // P = hi 2^64 + lo in [2^104, 2^106): keep its top 53 bits
+  const int top = (int)(hi >> 41);  // 1 when P >= 2^105
+  const int s = 52 + top;
+  const unsigned long long m = (hi << (64 - s)) | (lo >> s);  // in [2^52, 2^53)
+  const unsigned long long rem = lo & ((1ull << s) - 1ull), half = 1ull << (s - 1);
+  const unsigned long long up = (rem + (m & 1ull) > half) ? 1ull : 0ull;  // nearest, ties to even
+  // the implicit bit of m adds one to the exponent field, and a rounding carry
+  // out of m (m + up = 2^53) moves on into it
+  const unsigned long long r = ((unsigned long long)(e0 + top - 1) << 52) + m + up;
+  return __longlong_as_double((long long)(r | ((ua ^ ub) & 0x8000000000000000ull)));
+}
+
 // 1/sqrt(x) for a positive double x, accurate to about one ulp.
-// Default: FP32 seed (22.9 bits) and one third-order FP64 step (two FP64
-// multiplies and three FMAs, against two and four for two Newton steps
-// y <- y + y (1/2 - (x/2) y^2), the TOR_RSQRT_CUBIC=0 alternative; 3% faster
-// walk at k = 32).  With TOR_RSQRT_DF, the seed comes instead
+// Default: a seed of at least 20 bits (TOR_RSQRT_SEED) and one third-order
+// FP64 step (two FP64 multiplies and three FMAs, against two and four for two
+// Newton steps y <- y + y (1/2 - (x/2) y^2), the TOR_RSQRT_CUBIC=0
+// alternative; 3% faster walk at k = 32).  From a seed with relative error
+// 2^-20 the step's truncation error (5/16) e^3, e = 1 - x y^2 < 2^-18.9, stays
+// below 2^-58.  With TOR_RSQRT_DF, the seed comes instead
 // from a double-float step: x is split EXACTLY into two floats by integer operations on its bit
 // pattern, x = xh + xl (xh = the top 24 mantissa bits); one Newton step
 // y1 = y0 + y0 e / 2, e = 1 - x y0^2, is taken in FP32 arithmetic with the
@@ -163,9 +215,18 @@ __device__ __forceinline__ double rsqrt_fp64(double x) {
     y = (double)y0 + (double)c;
     const double r = fma(-dmul(hx, y), y, 0.5);
     y = fma(y, r, y);
-  } else {  // 23-bit FP32 seed (or the FP64 approximation out of float range), two FP64 steps
-    const float xf = __double2float_rn(x);
-    if (xf > 1e-30f && xf < 1e30f) {
+  } else {  // the seed (out of float range: the FP64 approximation), then the FP64 step(s)
+    if (TOR_RSQRT_SEED == 2) {
+      asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    } else if (TOR_RSQRT_SEED == 1 && ex >= 1023 - 99 && ex <= 1023 + 99) {
+      // x -> float and the float seed -> double by exponent rebias on the bit
+      // patterns (x's mantissa truncated to 23 bits), integer operations only
+      const float xf = __int_as_float((int)(((unsigned long long)bx >> 29) - (896ull << 23)));
+      float yf;
+      asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
+      y = __longlong_as_double(((long long)(unsigned)__float_as_int(yf) << 29) + (896ll << 52));
+    } else if (TOR_RSQRT_SEED == 0 && __double2float_rn(x) > 1e-30f && __double2float_rn(x) < 1e30f) {
+      const float xf = __double2float_rn(x);
       float yf;
       asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
       y = (double)yf;
@@ -174,8 +235,9 @@ __device__ __forceinline__ double rsqrt_fp64(double x) {
     }
     if (TOR_RSQRT_CUBIC) {
       // one third-order step: with e = 1 - x y^2, x^-1/2 = y (1 - e)^-1/2 =
-      // y (1 + e/2 + 3 e^2/8 + O(e^3)) by the binomial series; from the 22.9-bit
-      // seed the truncation error is about (5/16) e^3 < 2^-66, below FP64 rounding
+      // y (1 + e/2 + 3 e^2/8 + O(e^3)) by the binomial series; from a seed of
+      // relative error d <= 2^-20, |e| <= 2d + d^2 < 2^-18.9 and the truncation
+      // error is about (5/16) |e|^3 < 2^-58, below FP64 rounding
       const double e = fma(-dmul(x, y), y, 1.0);
       const double p = fma(e, 0.375, 0.5);
       y = fma(dmul(y, e), p, y);
@@ -210,16 +272,26 @@ struct TierF64 {
     return (u - 1ull) >= 0x7FEFFFFFFFFFFFFFull;
   }
   __device__ static __forceinline__ T rsqrt(T x, int &) { return rsqrt_fp64(x); }
-  __device__ static __forceinline__ T mul(T a, T b, int &) { return dmul(a, b); }
+  __device__ static __forceinline__ T mul(T a, T b, int &) { return (TOR_F64_IMUL & 4) ? dmul_i(a, b) : dmul(a, b); }
   // pivot coefficients: S_cc^-1 = [[al, -be], [-be, de]] with inv = y^2 = 1/det2
   __device__ static __forceinline__ void coef(T a, T b, T d, T y, T &al, T &be, T &de, int &) {
-    const T inv = dmul(y, y);
-    al = dmul(d, inv); be = dmul(b, inv); de = dmul(a, inv);
+    if (TOR_F64_IMUL & 2) {
+      const T inv = dmul_i(y, y);
+      al = dmul_i(d, inv); be = dmul_i(b, inv); de = dmul_i(a, inv);
+    } else {
+      const T inv = dmul(y, y);
+      al = dmul(d, inv); be = dmul(b, inv); de = dmul(a, inv);
+    }
   }
   // v = S_cc^-1 u
   __device__ static __forceinline__ void vrow(T al, T be, T de, T ux, T up, T &vx, T &vp, int &) {
-    vx = fma(al, ux, -dmul(be, up));
-    vp = fma(de, up, -dmul(be, ux));
+    if (TOR_F64_IMUL & 1) {
+      vx = fma(al, ux, -dmul_i(be, up));
+      vp = fma(de, up, -dmul_i(be, ux));
+    } else {
+      vx = fma(al, ux, -dmul(be, up));
+      vp = fma(de, up, -dmul(be, ux));
+    }
   }
   __device__ static __forceinline__ T upd(T s, T vx, T ux, T vp, T up, int &) {
     return fma(-vp, up, fma(-vx, ux, s));

@@ -38,6 +38,13 @@ namespace tor {
 #ifndef FX9_MINB
 #define FX9_MINB 3
 #endif
+// 1: the three coefficient products and the two pivot-row products each
+// share one inlined copy (operands selected per pass): about 75 KB of code
+// against 81 KB, 1853.8 against 1862.5 ms for the k = 32 walk; 0: one copy
+// per product
+#ifndef FX9_COMPACT
+#define FX9_COMPACT 1
+#endif
 // the reciprocal square root's seed: 1 = double-double (about 100 bits) and
 // one fixed-point Newton step (2.28 G subset-dets/s at k = 32), 0 = FP64 and
 // two steps (2.20)
@@ -234,7 +241,28 @@ __device__ void fx9_walk_chunk(const Src &src, int k, int r1, unsigned long long
         // S_child = S[<c] - u D^-1 u^T with D^-1 = inv [[d, -b], [-b, a]], inv = y^2
         const fx9 inv = fx9_mul(y, y, ovf);
         const fx9 ninv = fx9_neg(inv);
+#if FX9_COMPACT
+        // one inlined product for the three coefficients (operands chosen per pass)
+        fx9 nal, nde, be;
+#pragma unroll 1
+        for (int q = 0; q < 3; ++q) {
+          fx9 x, w;
+#pragma unroll
+          for (int l = 0; l < 9; ++l) {
+            x.l[l] = (q == 0) ? d.l[l] : (q == 1) ? a.l[l] : b.l[l];
+            w.l[l] = (q == 2) ? inv.l[l] : ninv.l[l];
+          }
+          const fx9 pr = fx9_mul(x, w, ovf);
+#pragma unroll
+          for (int l = 0; l < 9; ++l) {
+            nal.l[l] = (q == 0) ? pr.l[l] : nal.l[l];
+            nde.l[l] = (q == 1) ? pr.l[l] : nde.l[l];
+            be.l[l] = (q == 2) ? pr.l[l] : be.l[l];
+          }
+        }
+#else
         const fx9 nal = fx9_mul(d, ninv, ovf), nde = fx9_mul(a, ninv, ovf), be = fx9_mul(b, inv, ovf);
+#endif
         const bool last = (cur == r - 1) || skip > 0;
         Fx9Mem C;
         int coff, cins;
@@ -254,8 +282,28 @@ __device__ void fx9_walk_chunk(const Src &src, int k, int r1, unsigned long long
         for (int i = 0; i < 2 * cur; ++i) {
           const fx9 uxi = P.ld(cx + i), upi = P.ld(cp + i);
           // -v_i = -(D^-1 u_i): x part be up - al ux, p part be ux - de up
+#if FX9_COMPACT
+          fx9 nvx, nvp;
+#pragma unroll 1
+          for (int q = 0; q < 2; ++q) {
+            fx9 u1, c2, u2;
+#pragma unroll
+            for (int l = 0; l < 9; ++l) {
+              u1.l[l] = q ? uxi.l[l] : upi.l[l];
+              c2.l[l] = q ? nde.l[l] : nal.l[l];
+              u2.l[l] = q ? upi.l[l] : uxi.l[l];
+            }
+            const fx9 v = fx9_dot2(be, u1, c2, u2, ovf);
+#pragma unroll
+            for (int l = 0; l < 9; ++l) {
+              nvx.l[l] = q ? nvx.l[l] : v.l[l];
+              nvp.l[l] = q ? v.l[l] : nvp.l[l];
+            }
+          }
+#else
           const fx9 nvx = fx9_dot2(be, upi, nal, uxi, ovf);
           const fx9 nvp = fx9_dot2(be, uxi, nde, upi, ovf);
+#endif
           const int row = ix(i, 0);
 #pragma unroll 1
           for (int j = 0; j <= i; ++j)
