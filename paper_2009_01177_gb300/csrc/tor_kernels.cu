@@ -101,7 +101,10 @@ k_dfs(const double *__restrict__ B, const double *__restrict__ Blo, int k, const
 }
 
 // The 256-bit-class tier: the fx9 walk (tor_fx9.cuh) over the same chunk
-// segments; per-thread 512-bit totals, exact block sums of 16 limbs.
+// segments; per-thread 512-bit totals, exact block sums of 16 limbs.  The
+// totals live in shared memory behind the mini-stacks ([limb][thread]), read
+// and written once per chunk, so that their 32 registers are free during the
+// walk.
 __global__ void __launch_bounds__(128, FX9_MINB)
 k_dfs_fx9(const double *__restrict__ B, const double *__restrict__ Blo, int k, const WalkSegs seg,
           char *__restrict__ scratch, unsigned long long *__restrict__ block_part,
@@ -109,12 +112,14 @@ k_dfs_fx9(const double *__restrict__ B, const double *__restrict__ Blo, int k, c
   extern __shared__ int4 smem_fx9[];
   const unsigned st = gridDim.x * blockDim.x;
   const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned bd = blockDim.x, tid = threadIdx.x;
   const Fx9Mem G{scratch, st, gtid};
-  const Fx9Mem Q{reinterpret_cast<char *>(smem_fx9), blockDim.x, threadIdx.x};
+  const Fx9Mem Q{reinterpret_cast<char *>(smem_fx9), bd, tid};
+  unsigned long long *tot = reinterpret_cast<unsigned long long *>(
+      reinterpret_cast<char *>(smem_fx9) + (size_t)fx9_smem_entries(FX9_RSMEM) * 36 * bd);
   const SrcPrepped src{B, Blo, 2 * k};
-  Fx512 tot_tor, tot_sabs;
-  fx_zero(tot_tor);
-  fx_zero(tot_sabs);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) tot[i * bd + tid] = 0ull;
   int flags = 0;
 #pragma unroll 1
   for (int g = 0; g < 2; ++g) {
@@ -131,25 +136,30 @@ k_dfs_fx9(const double *__restrict__ B, const double *__restrict__ Blo, int k, c
 #pragma unroll
         for (int i = 0; i < 8; ++i) { o[i] = ct.w[i]; o[8 + i] = cs.w[i]; }
       }
-      fx_add(tot_tor, ct);
-      fx_add(tot_sabs, cs);
+      Fx512 t;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) t.w[i] = tot[i * bd + tid];
+      fx_add(t, ct);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) tot[i * bd + tid] = t.w[i];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) t.w[i] = tot[(8 + i) * bd + tid];
+      fx_add(t, cs);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) tot[(8 + i) * bd + tid] = t.w[i];
       flags |= A.flags;
     }
   }
-  __syncthreads();
-  unsigned long long(*red)[16] = reinterpret_cast<unsigned long long(*)[16]>(smem_fx9);
-#pragma unroll
-  for (int i = 0; i < 8; ++i) { red[threadIdx.x][i] = tot_tor.w[i]; red[threadIdx.x][8 + i] = tot_sabs.w[i]; }
   if (flags) atomicOr(status, flags);
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     Fx512 a, b, x;
     fx_zero(a);
     fx_zero(b);
-    for (int t2 = 0; t2 < (int)blockDim.x; ++t2) {
-      for (int i = 0; i < 8; ++i) x.w[i] = red[t2][i];
+    for (unsigned t2 = 0; t2 < bd; ++t2) {
+      for (int i = 0; i < 8; ++i) x.w[i] = tot[i * bd + t2];
       fx_add(a, x);
-      for (int i = 0; i < 8; ++i) x.w[i] = red[t2][8 + i];
+      for (int i = 0; i < 8; ++i) x.w[i] = tot[(8 + i) * bd + t2];
       fx_add(b, x);
     }
     for (int i = 0; i < 8; ++i) {
@@ -159,11 +169,10 @@ k_dfs_fx9(const double *__restrict__ B, const double *__restrict__ Blo, int k, c
   }
 }
 
-// shared memory of a fx9 walk block: the per-thread mini-stacks (at least the
-// reduction's 128 bytes per thread)
+// shared memory of a fx9 walk block: the per-thread mini-stacks and the
+// per-thread 512-bit totals (128 bytes)
 static size_t fx9_smem_bytes(int block) {
-  const size_t slot = (size_t)fx9_smem_entries(FX9_RSMEM) * 36;
-  return (slot > 128 ? slot : 128) * (size_t)block;
+  return ((size_t)fx9_smem_entries(FX9_RSMEM) * 36 + 128) * (size_t)block;
 }
 
 // sum of the blocks' partials (2 L limbs each) -> tor_result
