@@ -251,6 +251,10 @@ k_batch_walk_fx9(BatchInput in, BatchPlan p, char *__restrict__ scratch) {
   const unsigned long long end = p.range[2 * t + 1];
   const int jlo = (int)p.counts[t - 1];
   const int jhi = (int)p.counts[t];
+#if FX9_SUMS_SMEM
+  long long *colsum = reinterpret_cast<long long *>(reinterpret_cast<char *>(smem_b9) +
+                                                    (size_t)fx9_smem_entries(FX9_RSMEM) * 36 * blockDim.x);
+#endif
   while (true) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(p.counter + t, 32ull);
@@ -266,7 +270,11 @@ k_batch_walk_fx9(BatchInput in, BatchPlan p, char *__restrict__ scratch) {
       const int i = p.order[a];
       const unsigned long long c = item - p.item_off[a];
       const int ki = in.k[i], r1 = p.r1[i];
+#if FX9_SUMS_SMEM
+      Fx9SumsShared A{colsum + threadIdx.x, blockDim.x, 0};
+#else
       Fx9Sums A;
+#endif
       A.zero();
       if constexpr (PAT) {
         unsigned char gm[64];
@@ -290,7 +298,7 @@ k_batch_walk_fx9(BatchInput in, BatchPlan p, char *__restrict__ scratch) {
 }
 
 static size_t fx9_batch_smem(int block) {
-  const size_t slot = (size_t)fx9_smem_entries(FX9_RSMEM) * 36;
+  const size_t slot = (size_t)fx9_smem_entries(FX9_RSMEM) * 36 + (FX9_SUMS_SMEM ? 104 : 0);
   return slot * (size_t)block;
 }
 

@@ -51,6 +51,13 @@ namespace tor {
 #ifndef FX9_DDSEED
 #define FX9_DDSEED 1
 #endif
+// 1: the walk kernels keep each chunk's column sums in shared memory
+// (Fx9SumsShared) instead of 26 registers: spills 176 -> 20 bytes, the k = 32
+// walk 1808.0 -> 1759.3 ms and an fx256 batch 2.35 -> 2.41 G subset-dets/s,
+// same bits; 0: in registers (Fx9Sums)
+#ifndef FX9_SUMS_SMEM
+#define FX9_SUMS_SMEM 1
+#endif
 
 // entries of the shared-memory mini-stack: a node of RSMEM modes and the chain
 // of its largest non-last descendants (RSMEM - 2, RSMEM - 4, ...)
@@ -99,6 +106,30 @@ struct Fx9Sums {
 #pragma unroll
     for (int m = 0; m < 4; ++m) sabs[m] += t.l[m + 5];
   }
+  __device__ __forceinline__ long long tor_col(int m) const { return tor[m]; }
+  __device__ __forceinline__ long long sabs_col(int m) const { return sabs[m]; }
+};
+
+// The same column sums in shared memory, [column][thread] with stride st.
+// Each thread owns its columns (plain loads and stores), and the 26 registers
+// the sums would hold stay free for the walk.
+struct Fx9SumsShared {
+  long long *s;  // this thread's column 0
+  unsigned st;
+  int flags;
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int m = 0; m < 13; ++m) s[m * st] = 0;
+    flags = 0;
+  }
+  __device__ __forceinline__ void add(const fx9 &t, bool neg) {
+#pragma unroll
+    for (int m = 0; m < 9; ++m) s[m * st] += neg ? -(long long)t.l[m] : (long long)t.l[m];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) s[(9 + m) * st] += t.l[m + 5];
+  }
+  __device__ __forceinline__ long long tor_col(int m) const { return s[m * st]; }
+  __device__ __forceinline__ long long sabs_col(int m) const { return s[(9 + m) * st]; }
 };
 
 // column sums -> 512-bit two's complement with 256 fraction bits, exactly:
@@ -114,13 +145,14 @@ __device__ __forceinline__ void fx9_fold_col(Fx512 &x, long long v, int shift) {
   fx_add(x, y);
 }
 
-static __device__ __noinline__ void fx9_fold(const Fx9Sums &S, Fx512 &tor_out, Fx512 &sabs_out) {
+template <class Sums>
+static __device__ __noinline__ void fx9_fold(const Sums &S, Fx512 &tor_out, Fx512 &sabs_out) {
   fx_zero(tor_out);
   fx_zero(sabs_out);
 #pragma unroll 1
-  for (int m = 0; m < 9; ++m) fx9_fold_col(tor_out, S.tor[m], 29 * m + 53);
+  for (int m = 0; m < 9; ++m) fx9_fold_col(tor_out, S.tor_col(m), 29 * m + 53);
 #pragma unroll 1
-  for (int m = 0; m < 4; ++m) fx9_fold_col(sabs_out, S.sabs[m], 29 * (m + 5) + 53);
+  for (int m = 0; m < 4; ++m) fx9_fold_col(sabs_out, S.sabs_col(m), 29 * (m + 5) + 53);
 }
 
 // B = I - O entries as normalised fx9, exactly (up to bits below 2^-203): from
@@ -138,10 +170,10 @@ __device__ __forceinline__ fx9 fx9_entry(const Src &src, int row, int col, int &
 
 // One chunk: the subsets whose high modes r1..k-1 are fixed by the bits of c.
 // G: this thread's global stack (root and large nodes); Q: its shared-memory
-// mini-stack.  Adds the chunk's terms to A.
-template <class Src>
+// mini-stack.  Adds the chunk's terms to A (Fx9Sums or Fx9SumsShared).
+template <class Src, class Sums>
 __device__ void fx9_walk_chunk(const Src &src, int k, int r1, unsigned long long c, const Fx9Mem &G,
-                               const Fx9Mem &Q, Fx9Sums &A) {
+                               const Fx9Mem &Q, Sums &A) {
   int ovf = 0;
   // ---- gather B over the fixed modes P0 (in Z) followed by the low modes
   // the lanes that walk a chunk of the same depth r1 now (the same number of

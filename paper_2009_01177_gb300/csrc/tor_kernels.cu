@@ -117,6 +117,9 @@ k_dfs_fx9(const double *__restrict__ B, const double *__restrict__ Blo, int k, c
   const Fx9Mem Q{reinterpret_cast<char *>(smem_fx9), bd, tid};
   unsigned long long *tot = reinterpret_cast<unsigned long long *>(
       reinterpret_cast<char *>(smem_fx9) + (size_t)fx9_smem_entries(FX9_RSMEM) * 36 * bd);
+#if FX9_SUMS_SMEM
+  long long *colsum = reinterpret_cast<long long *>(tot + 16 * bd);  // the chunk's column sums
+#endif
   const SrcPrepped src{B, Blo, 2 * k};
 #pragma unroll
   for (int i = 0; i < 16; ++i) tot[i * bd + tid] = 0ull;
@@ -126,7 +129,11 @@ k_dfs_fx9(const double *__restrict__ B, const double *__restrict__ Blo, int k, c
     const int r1 = seg.r1[g];
 #pragma unroll 1
     for (unsigned long long c = seg.c0[g] + gtid; c < seg.c1[g]; c += st) {
+#if FX9_SUMS_SMEM
+      Fx9SumsShared A{colsum + tid, bd, 0};
+#else
       Fx9Sums A;
+#endif
       A.zero();
       fx9_walk_chunk(src, k, r1, c, G, Q, A);
       Fx512 ct, cs;
@@ -169,10 +176,10 @@ k_dfs_fx9(const double *__restrict__ B, const double *__restrict__ Blo, int k, c
   }
 }
 
-// shared memory of a fx9 walk block: the per-thread mini-stacks and the
-// per-thread 512-bit totals (128 bytes)
+// shared memory of a fx9 walk block: the per-thread mini-stacks, the
+// per-thread 512-bit totals (128 bytes) and the chunk's column sums (104 bytes)
 static size_t fx9_smem_bytes(int block) {
-  return ((size_t)fx9_smem_entries(FX9_RSMEM) * 36 + 128) * (size_t)block;
+  return ((size_t)fx9_smem_entries(FX9_RSMEM) * 36 + 128 + (FX9_SUMS_SMEM ? 104 : 0)) * (size_t)block;
 }
 
 // sum of the blocks' partials (2 L limbs each) -> tor_result
