@@ -545,7 +545,7 @@ def run_batch(args):
     ts = e0.elapsed_time(e1) / 1e3
     res1 = tor.results_from_tensor(o1, n)
     agree = sum(abs(a.value - b.value) <= a.err_est + b.err_est for a, b, t in zip(res, res1, tiers) if t != "none")
-    line = {"metric": "batched Tor/s (4096 patterns, k in [8,30]) at tol", "value": n / tb, "unit": "Tor/s",
+    line = {"metric": f"batched Tor/s ({n} patterns, k in [8,30]) at tol", "value": n / tb, "unit": "Tor/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tb,
             "higher_is_better": True, "dtype": "auto: " + ", ".join(sorted(set(tiers))), "data": "synthetic",
             "config": {"workload": f"{n} click patterns of a synthetic M=100 lossy GBS state "
