@@ -53,10 +53,11 @@ def test_reduced_state_prefix_probabilities_are_marginals(ctx):
         assert np.max(np.abs(pj - marg)) < 1e-12, j
 
 
-def test_chain_rule_samples_follow_the_exact_distribution(ctx):
+@pytest.mark.parametrize("form", ["noclick", "click"])
+def test_chain_rule_samples_follow_the_exact_distribution(ctx, form):
     st = gi.lossy_gbs_state(10, 0.5, 1.0, 0.5, 72)
     p = table_p(ctx, st)
-    pats = chainrule.sample(ctx, st.Sigma, 60000, seed=72, prec="auto", tol=1e-9)
+    pats = chainrule.sample(ctx, st.Sigma, 60000, seed=72, prec="auto", tol=1e-9, form=form)
     assert pats.shape == (60000, 10)
     assert g_test_pvalue(p, pats) > 1e-4
     assert chainrule.tv_against_table(p, pats) < 0.1
