@@ -100,8 +100,9 @@ __device__ __forceinline__ void fx_add_signed(Fx256 &acc, double x, bool neg, in
 // instruction (measured max relative error 2^-20.05 over [2^-60, 2^60)),
 // 1 = the FP32 one with x and the seed moved between FP64 and FP32 by exponent
 // rebias on the bit patterns, 0 = the FP32 one with conversion instructions.
-// On GB300 the FP64<->FP32 conversions issue to the FP64 pipe: 0 measured
-// 291.9 ms for the k = 32 FP64 walk, 1 275.2 ms and 2 273.9 ms.
+// Taking the FP64<->FP32 conversions out of the pivot's dependency chain pays
+// on GB300: 0 measured 291.9 ms for the k = 32 FP64 walk, 1 275.2 ms and
+// 2 273.9 ms.
 #ifndef TOR_RSQRT_SEED
 #define TOR_RSQRT_SEED 2
 #endif

@@ -102,9 +102,10 @@ k_dfs(const double *__restrict__ B, const double *__restrict__ Blo, int k, const
 
 // The 256-bit-class tier: the fx9 walk (tor_fx9.cuh) over the same chunk
 // segments; per-thread 512-bit totals, exact block sums of 16 limbs.  The
-// totals live in shared memory behind the mini-stacks ([limb][thread]), read
-// and written once per chunk, so that their 32 registers are free during the
-// walk.
+// totals (read and written once per chunk) and, with FX9_SUMS_SMEM, each
+// chunk's column sums live in shared memory behind the mini-stacks
+// ([word][thread]), so that the walk's registers hold only the nodes it
+// updates.
 __global__ void __launch_bounds__(128, FX9_MINB)
 k_dfs_fx9(const double *__restrict__ B, const double *__restrict__ Blo, int k, const WalkSegs seg,
           char *__restrict__ scratch, unsigned long long *__restrict__ block_part,
