@@ -507,6 +507,28 @@ def test_maximum_k_sampled_chunk(ctx, prec):
     assert abs(got - ref_t) <= 4 * k * Fraction(u) * ref_s + ref_s * Fraction(1, 2 ** 190)
 
 
+@pytest.mark.parametrize("k", [40, 50])
+def test_adaptive_instances_sampled_chunks_at_bench_depth(ctx, k):
+    # the adaptive-precision workload (M = 100, r ~ U[0.8, 1.4], eta = 0.3, seed 3; nested
+    # patterns of k = 40 and 50 clicks, pattern seed 1003) at the depth the bench's 256-bit
+    # windows walk (17 walked modes per chunk): the chunk whose only fixed mode in Z is the
+    # highest, and one with every other fixed mode in Z, against the oracle's mask ranges
+    from paper_2009_01177_gb300.tor import limbs_to_int
+    st = gi.lossy_gbs_state(100, 0.8, 1.4, 0.3, 3)
+    pat = gi.random_pattern(100, 50, 1003)
+    O = gi.select(st.O, pat[:k])
+    r1 = 17
+    d = k - r1
+    for c in (1 << (d - 1), 0x5555555555555555 & ((1 << d) - 1)):
+        ref_t, ref_s = oracle.tor_exact(O, c << r1, (c + 1) << r1)
+        part = ctx.chunks(dev(O), d, c, c + 1, prec="fx256").cpu().numpy()[0]
+        L = part.size // 2
+        got = Fraction(limbs_to_int(part[:L]), 1 << (32 * L))
+        sabs = Fraction(limbs_to_int(part[L:]), 1 << (32 * L))
+        assert abs(sabs - ref_s) <= Fraction(1e-12) * ref_s, c
+        assert abs(got - ref_t) <= 4 * k * Fraction(2.0 ** -196) * ref_s + ref_s * Fraction(1, 2 ** 190), c
+
+
 def test_chunk_depth_above_the_old_limit_and_k_limits(ctx, cuda_lib):
     st, pat, O = gi.workload_m100(64)
     Od = dev(O)
