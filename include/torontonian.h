@@ -277,6 +277,20 @@ int tor_fx256_fma2(const int32_t *s_dev, const int32_t *a1_dev, const int32_t *b
  * GPU needed). */
 int tor_fixed_to_result(const uint64_t *limbs, int k, int tier, tor_result *out);
 
+/* tor_sum_partials: the exact sum of n fixed-point pairs as written by
+ * tor_chunks, the reduction over ranks that closes Algorithm 1 (each rank's
+ * partial sum of Eq. 2's terms; Sec. 5.1-5.2 fixed point, so the sum is exact
+ * and independent of the order).  Host code, no GPU needed.
+ *   parts  host  n x 2L little-endian uint64 limbs per pair: the signed sum
+ *                (L limbs, two's complement), then the sum of terms (L limbs);
+ *                L = 8 for TOR_PREC_FX256, else 4.
+ *   n           number of pairs, >= 0 (n = 0 writes zeros).
+ *   tier        the tier that wrote them (TOR_PREC_FP64 .. TOR_PREC_FX256).
+ *   out    host  2L limbs: both sums modulo 2^(64 L), caller-owned; it may
+ *                alias parts' first pair.
+ * TOR_EINVAL for null pointers, n < 0 or a bad tier. */
+int tor_sum_partials(const uint64_t *parts, int n, int tier, uint64_t *out);
+
 /*
  * tor_batch: Tor of n matrices of different k (e.g. the patterns a sampler
  * proposes), each by Eq. 2 (Sec. 3.1): the alternating sum over all 2^k_i

@@ -6,7 +6,7 @@ chunk range [r 2^d / R, (r+1) 2^d / R) with tor_chunks and the ranks exchange
 one fixed-point pair each (256-bit, or 512-bit for the 256-bit fixed-point
 tier).  Those partials add exactly (integer addition), so the gathered total
 is bit-identical to a single-GPU run.  The exchange is the only collective; it
-moves 64 (or 96) bytes per rank.
+moves 64 (or 128) bytes per rank.
 """
 from __future__ import annotations
 
@@ -44,18 +44,19 @@ def ints_to_limbs(lo: int, hi: int, limbs: int = 8) -> np.ndarray:
 
 
 def sum_partials(rows) -> np.ndarray:
-    """Exact sum of several partials (rows of an (n, 8) or (n, 16) array)."""
+    """Exact sum of several partials (rows of an (n, 8) or (n, 16) array) by the library's
+    tor_sum_partials; 16 limbs are the 256-bit tier's pairs, 8 any other tier's."""
     rows = np.asarray(rows)
     limbs = rows.shape[-1] if rows.ndim > 1 else rows.size
-    lo = hi = 0
-    for r in rows.reshape(-1, limbs):
-        a, b = limbs_to_ints(r)
-        lo, hi = lo + a, hi + b
-    return ints_to_limbs(lo, hi, limbs)
+    if limbs not in (8, 16):
+        raise ValueError(f"partials have 8 or 16 limbs, got {limbs}")
+    from . import tor
+    return tor.sum_partials(rows.reshape(-1, limbs), "fx256" if limbs == 16 else "fp64")
 
 
 def gather_partials(local, group=None) -> np.ndarray:
-    """All-gather each rank's 8-limb partial and add them exactly (any backend)."""
+    """All-gather each rank's partial (8 limbs, or 16 for the 256-bit tier) and add them exactly
+    (any backend)."""
     import torch
     import torch.distributed as dist
     world = dist.get_world_size(group)

@@ -92,6 +92,7 @@ SIGNATURES = {
     "tor_single_async": (_I, [_VP, _VP, _I, _I, _I, _I, _VP, _VP]),
     "tor_chunks": (_I, [_VP, _VP, _I, _I, _I, _I, _I, _U64, _U64, _VP, _VP]),
     "tor_fixed_to_result": (_I, [ctypes.POINTER(_U64), _I, _I, ctypes.POINTER(TorResultC)]),
+    "tor_sum_partials": (_I, [ctypes.POINTER(_U64), _I, _I, ctypes.POINTER(_U64)]),
     "tor_fx256_fma2": (_I, [_VP, _VP, _VP, _VP, _VP, _I, _VP, _VP, _VP]),
     "tor_levels_workspace": (_I, [_I, _I, ctypes.POINTER(ctypes.c_size_t)]),
     "tor_levels": (_I, [_VP, _I, _I, _I, _I, ctypes.POINTER(_I), _VP, ctypes.c_size_t, _VP, _VP]),
@@ -412,6 +413,18 @@ def fixed_to_result(limbs, k: int, tier: str = "fp64") -> TorResult:
     out = TorResultC()
     _check(load_library().tor_fixed_to_result(arr, k, _PREC[tier], ctypes.byref(out)))
     return TorResult.from_c(out)
+
+
+def sum_partials(rows, tier: str) -> "np.ndarray":
+    """tor_sum_partials: the exact sum of partial-sum pairs (rows of 2 L uint64 limbs, L = 8 for
+    fx256, else 4) as one pair of 2 L limbs."""
+    import numpy as np
+    n_limbs = partial_limbs(tier)
+    rows = np.ascontiguousarray(np.asarray(rows).astype(np.uint64, copy=False).reshape(-1, n_limbs))
+    out = np.zeros(n_limbs, dtype=np.uint64)
+    _check(load_library().tor_sum_partials(rows.ctypes.data_as(ctypes.POINTER(_U64)), rows.shape[0],
+                                           _PREC[tier], out.ctypes.data_as(ctypes.POINTER(_U64))))
+    return out
 
 
 def levels(O: torch.Tensor, prec: str = "fp64", level_prec=None, layout: str = "xxpp", stream=None) -> TorResult:

@@ -103,6 +103,43 @@ def test_shard_sums_of_512_bit_partials():
     assert lo == (3 - (1 << 400)) % (1 << 512) and hi == (1 << 400) + 7
 
 
+@pytest.mark.parametrize("tier", ["fp64", "fx256"])
+def test_library_sum_of_partials_is_the_big_integer_sum(lib, tier):
+    # tor_sum_partials (host code) against Python integers: signed sums that wrap and carry
+    # across every limb, both widths, n = 0 and n = 1
+    import random
+    from paper_2009_01177_gb300 import shard, tor
+    tor.load_library()
+    n_limbs = tor.partial_limbs(tier)
+    L = n_limbs // 2
+    rng = random.Random(11)
+    rows, lo, hi = [], 0, 0
+    for i in range(64):
+        a = rng.getrandbits(64 * L) - (1 << (64 * L - 1)) if i % 3 else (1 << (64 * L)) - 1
+        b = rng.getrandbits(64 * L - 8)
+        rows.append(shard.ints_to_limbs(a, b, limbs=n_limbs))
+        lo, hi = lo + a, hi + b
+    got = tor.sum_partials(np.stack(rows), tier)
+    assert np.array_equal(got, shard.ints_to_limbs(lo, hi, limbs=n_limbs))
+    assert np.array_equal(tor.sum_partials(np.zeros((0, n_limbs), dtype=np.uint64), tier),
+                          np.zeros(n_limbs, dtype=np.uint64))
+    assert np.array_equal(tor.sum_partials(rows[5], tier), rows[5])
+
+
+def test_library_sum_of_partials_refuses_bad_arguments(lib):
+    from paper_2009_01177_gb300 import tor
+    tor.load_library()
+    L = tor._lib
+    buf = (ctypes.c_uint64 * 16)()
+    EINVAL = tor.TOR_EINVAL
+    assert L.tor_sum_partials(None, 1, tor.PREC_FP64, buf) == EINVAL
+    assert L.tor_sum_partials(buf, 1, tor.PREC_FP64, None) == EINVAL
+    assert L.tor_sum_partials(buf, -1, tor.PREC_FP64, buf) == EINVAL
+    assert L.tor_sum_partials(buf, 1, tor.PREC_FX256 + 1, buf) == EINVAL
+    assert L.tor_sum_partials(buf, 1, tor.PREC_AUTO, buf) == EINVAL
+    assert "tier" in tor._lib.tor_last_error().decode()
+
+
 def test_bad_arguments_are_refused_before_any_device_call(lib):
     # every check below returns before the library touches CUDA, so it runs without a GPU
     from paper_2009_01177_gb300 import tor
