@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtorontonian.so")
-SOURCES = ["tor_kernels.cu", "capi.cu", "tor_noalloc.cu", "tor_bounds.cu", "tor_batch.cu", "tor_mlp.cu",
+SOURCES = ["tor_kernels.cu", "capi.cu", "tor_partials.cu", "tor_noalloc.cu", "tor_bounds.cu", "tor_batch.cu", "tor_mlp.cu",
            "tor_mh.cu", "tor_table.cu", "tor_levels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -528,29 +528,6 @@ int tor_fixed_to_result(const uint64_t *limbs, int k, int tier, tor_result *out)
   return TOR_OK;
 }
 
-int tor_sum_partials(const uint64_t *parts, int n, int tier, uint64_t *out) {
-  if (!parts || !out) return fail(TOR_EINVAL, "null pointer");
-  if (n < 0) return fail(TOR_EINVAL, "n = %d < 0", n);
-  if (tier < TOR_PREC_FP64 || tier > TOR_PREC_FX256) return fail(TOR_EINVAL, "bad tier");
-  const int L = (tier == TOR_PREC_FX256) ? 8 : 4;
-  uint64_t acc[16] = {0};
-  for (int i = 0; i < n; ++i) {
-    const uint64_t *p = parts + (size_t)i * 2 * L;
-    for (int h = 0; h < 2; ++h) {  // the signed sum, then the sum of terms: L-limb adds with carry
-      uint64_t carry = 0;
-      for (int m = 0; m < L; ++m) {
-        const uint64_t a = acc[h * L + m], b = p[h * L + m];
-        const uint64_t s1 = a + b, c1 = s1 < a ? 1u : 0u;
-        const uint64_t s2 = s1 + carry, c2 = s2 < s1 ? 1u : 0u;
-        acc[h * L + m] = s2;
-        carry = c1 + c2;
-      }
-    }
-  }
-  for (int m = 0; m < 2 * L; ++m) out[m] = acc[m];
-  return TOR_OK;
-}
-
 static int batch_grid(const tor_ctx *ctx, int tier, bool patterns = false) {
   const int occ = tor::batch_walk_max_blocks_per_sm(tier, ctx->threads_per_block, patterns);
   return ctx->sms * (ctx->blocks_per_sm < occ ? ctx->blocks_per_sm : occ);
