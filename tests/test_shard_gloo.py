@@ -35,17 +35,18 @@ def _rank_main(rank, world, port, partials, out):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     lo, hi = shard.chunk_range(rank, world, len(partials))
-    local = shard.sum_partials(np.stack(partials[lo:hi])) if hi > lo else np.zeros(8, np.uint64)
+    local = shard.sum_partials(np.stack(partials[lo:hi])) if hi > lo else np.zeros(len(partials[0]), np.uint64)
     total = shard.gather_partials(local)
     out[rank] = [int(x) for x in total]
     dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_gather_exactly():
+@pytest.mark.parametrize("limbs", [8, 16])   # 256-bit pairs, and the 256-bit tier's 512-bit pairs
+def test_two_gloo_ranks_gather_exactly(limbs):
     rng = np.random.default_rng(1)
     # per-chunk partials as the GPU writes them: signed sums and sums of |t|
     vals = [int(rng.integers(-2**60, 2**60)) * (1 << 90) + int(rng.integers(0, 2**40)) for _ in range(37)]
-    partials = [shard.ints_to_limbs(v, abs(v)) for v in vals]
+    partials = [shard.ints_to_limbs(v, abs(v), limbs=limbs) for v in vals]
     ctx = mp.get_context("spawn")
     with ctx.Manager() as m:
         out = m.dict()
@@ -59,5 +60,5 @@ def test_two_gloo_ranks_gather_exactly():
         res = [out[0], out[1]]
     assert res[0] == res[1]
     lo, hi = shard.limbs_to_ints(np.array(res[0], dtype=np.uint64))
-    assert lo == sum(vals) % (1 << 256)
+    assert lo == sum(vals) % (1 << (32 * limbs))
     assert hi == sum(abs(v) for v in vals)
