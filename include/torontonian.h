@@ -34,8 +34,9 @@
  *
  * Accuracy
  *   Subset terms t_Z = 1/sqrt(det(I - O_Z)) are computed in the tier's
- *   arithmetic (FP64, or double-double) and summed EXACTLY in 256-bit
- *   fixed point, so the only error is the per-term rounding.  Each result
+ *   arithmetic (FP64, double-double, or 128- or 256-bit fixed point) and
+ *   summed EXACTLY in fixed point (256-bit; 512-bit for the 256-bit tier), so
+ *   the only error is the per-term rounding.  Each result
  *   carries sum_abs = sum_Z t_Z (condition number kappa = sum_abs/|Tor|) and
  *   err_est = gamma * u_tier * sum_abs, an a-posteriori bound on |error|.
  */
