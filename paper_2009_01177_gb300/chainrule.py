@@ -67,7 +67,9 @@ def sample(ctx, Sigma: np.ndarray, n: int, seed: int, k_min: int = 0, k_max: int
                 stats["torontonians"] = stats.get("torontonians", 0) + live.size
                 stats["subsets"] = stats.get("subsets", 0.0) + float((2.0 ** cand.sum(1)).sum())
             val, ok = evaluate(j, mats[j][0], cand)
-            logv = np.where(ok, np.log(np.where(ok, val, 1.0)), -np.inf) - 0.5 * mats[j][1]
+            if not np.all(ok):   # every p(S) of a Gaussian state is positive: a failure is an error
+                raise RuntimeError(f"{int((~np.asarray(ok)).sum())} prefix Torontonians failed at mode {j}")
+            logv = np.log(val) - 0.5 * mats[j][1]
             with np.errstate(divide="ignore", invalid="ignore"):
                 ratio = np.clip(np.exp(logv - logp[live]), 0.0, 1.0)
                 cond = ratio if form == "click" else 1.0 - ratio  # p(s_j = 1 | prefix)

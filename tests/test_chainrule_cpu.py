@@ -88,6 +88,20 @@ def test_click_window_is_the_conditional_distribution(state):
     assert chi2_pvalue(pc, pats) > 1e-4
 
 
+def test_a_failed_evaluation_is_an_error(state):
+    st, _ = state
+    inner = oracle_evaluator()
+
+    def failing(j, Oj, cand):
+        val, ok = inner(j, Oj, cand)
+        if j == 4:
+            ok = ok.copy()
+            ok[0] = False
+        return val, ok
+    with pytest.raises(RuntimeError, match="mode 4"):
+        chainrule.sample(None, st.Sigma, 100, seed=2, evaluate=failing)
+
+
 def test_unknown_form_is_rejected(state):
     st, _ = state
     with pytest.raises(ValueError):
