@@ -21,3 +21,11 @@ def cuda_lib():
         pytest.skip("no CUDA device")
     from paper_2009_01177_gb300 import tor
     return tor
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built_library():
+    """Compile the product library if it is missing or stale (nvcc only, no GPU needed), so CPU
+    tests of host code that goes through it (partial sums, conversions) run from a fresh tree."""
+    from paper_2009_01177_gb300 import build
+    build.build()
