@@ -15,6 +15,12 @@ def test_paper_flop_model_counts_one_solve_per_subset():
         direct = sum(comb(k, i) * (4 / 3 * (2 * i) ** 3 + (2 * i) ** 2 - 4 / 3 * (2 * i)) for i in range(1, k + 1))
         assert bench.paper_flops(k) == pytest.approx(direct, rel=1e-12)
     assert bench.paper_flops(1) == 12.0
+    # closed form by the binomial moments sum C(N,i) i = N 2^(N-1), sum C(N,i) i^2 = N (N+1) 2^(N-2)
+    # and sum C(N,i) i^3 = N^2 (N+3) 2^(N-3) (Eq. tflops summed over i)
+    for n in (2, 7, 32, 50):
+        closed = (32 / 3 * n * n * (n + 3) * 2.0 ** (n - 3) + 4 * n * (n + 1) * 2.0 ** (n - 2)
+                  - 8 / 3 * n * 2.0 ** (n - 1))
+        assert bench.paper_flops(n) == pytest.approx(closed, rel=1e-12)
 
 
 def test_hbm_peak_prefers_the_measured_file(tmp_path, monkeypatch):
